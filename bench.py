@@ -1,0 +1,344 @@
+"""Throughput of the batched coherent-fitness evaluation on one GB300 (or N, one rank per GPU).
+
+One step = one fcas_fitness call over the whole batch of particles of the 4-detector x 60-min
+@ 2048 Hz workload (7,372,800 samples zero-padded to 2^23, band 30-1000 Hz, 320 particles): sky
+geometry, fused template x data x delay phase, both FFT passes over t_c, antenna projection and
+argmax. ``value`` is particles evaluated per second over all ranks (weak scaling: every rank has
+its own data realisation and particle batch, no data-path collective).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
+
+``--impl reference`` times the FP64 CPU oracle on a bounded sample of the same workload.
+"""
+
+import argparse
+import glob
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synthdata as sd  # noqa: E402
+
+METRIC = "fitness evals/s (4 det x 60 min @2048 Hz, % HBM roofline); search time/data time"
+UNIT = "evals/s"
+PSO_EVALS = 8 * 40 * 2000          # 8 runs x 40 particles x 2000 iterations
+DATA_SECONDS = 3600.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=sd.C2.name)
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--cpu-sample", type=int, default=4, help="particles in the oracle CPU-baseline sample")
+    ap.add_argument("--particles", type=int, default=0, help="particles per GPU (0 = the workload's batch)")
+    ap.add_argument("--max-batch", type=int, default=0, help="particles per internal chunk (0 = automatic)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------------------------------- ranks
+class Ranks:
+    """Process-group plumbing: barrier and max/sum over ranks (gloo on CPU, nccl on GPUs)."""
+
+    def __init__(self, backend=None):
+        import torch
+        import torch.distributed as dist
+        self.dist = dist
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.on = self.world > 1 and backend != "none"
+        if self.on and not dist.is_initialized():
+            if backend is None:
+                backend = "nccl" if torch.cuda.is_available() else "gloo"
+            dist.init_process_group(backend=backend)
+        self.backend = dist.get_backend() if self.on else None
+
+    def _dev(self):
+        import torch
+        return torch.device("cuda", self.local) if self.backend == "nccl" else torch.device("cpu")
+
+    def barrier(self):
+        if self.on:
+            self.dist.barrier()
+
+    def reduce(self, value, op):
+        if not self.on:
+            return value
+        import torch
+        t = torch.tensor([float(value)], dtype=torch.float64, device=self._dev())
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX if op == "max" else self.dist.ReduceOp.SUM)
+        return float(t.item())
+
+
+def aggregate(ranks, local_units, local_seconds):
+    """Whole-job throughput: units summed over ranks / slowest rank's time."""
+    total = ranks.reduce(local_units, "sum")
+    slowest = ranks.reduce(local_seconds, "max")
+    return total / slowest, slowest
+
+
+# ------------------------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+# ------------------------------------------------------------------------------------------- roofline
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2002_02150_gb300", "csrc", "*"))):
+        h.update(open(p, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel, workload):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on the current kernels."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    e = d.get(workload, {}).get(kernel)
+    if not e or e.get("kernel_hash") != kernel_source_hash():
+        return None
+    return e.get("bytes_per_launch")
+
+
+# ------------------------------------------------------------------------------------------- workload
+def workload_inputs(w, rank, particles=0):
+    data = sd.make_dataset(w, seed=rank)
+    theta = sd.make_particles(w, n=particles or None, seed=rank)
+    return data, theta
+
+
+def bench_ours(args, ranks):
+    import torch
+    import paper_2002_02150_gb300 as fc
+
+    torch.cuda.set_device(ranks.local)
+    dev = torch.device("cuda", ranks.local)
+    w = sd.workload_by_name(args.workload)
+    data, theta = workload_inputs(w, ranks.rank, args.particles)
+    n = theta.shape[0]
+    ctx = fc.fcas_create(data["det"], data["psd"], data["data"], w.n_fft, w.fs, w.f_low, w.f_high, precision="fp32",
+                         max_batch=args.max_batch)
+    info = fc.fcas_get_info(ctx)
+    th = torch.tensor(theta, device=dev)
+    fit = torch.empty(n, dtype=torch.float64, device=dev)
+    tc = torch.empty(n, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        fc.fcas_fitness(ctx, th, fit, tc, stream=stream.cuda_stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    fc.fcas_profile_enable(ctx, True)
+    ranks.barrier()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(ranks.local)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    clock = clocks.stop()
+    ranks.barrier()
+    local_s = t0.elapsed_time(t1) / 1e3
+    kern = {k: fc.fcas_profile_read(ctx, k) for k in ("geometry", "pass_a", "pass_b", "reduce")}
+    fc.fcas_profile_enable(ctx, False)
+    value, slowest = aggregate(ranks, n * args.steps, local_s)
+
+    # roofline of the dominant kernel: algorithmic bytes per launch / mean launch time
+    d, nn, nband = info["n_det"], info["n_fft"], info["n_band"]
+    chunks_per_step = -(-n // info["chunk"])
+    parts = [min(info["chunk"], n - c * info["chunk"]) for c in range(chunks_per_step)]
+    mean_p = sum(parts) / len(parts)
+    algo = {"pass_a": mean_p * d * nn * 8 + d * nband * 8, "pass_b": mean_p * d * nn * 8}
+    dom = max(("pass_a", "pass_b"), key=lambda k: kern[k][0])
+    ms, launches = kern[dom]
+    achieved = algo[dom] / (ms / launches / 1e3) / 1e9
+    peak, peak_kind = measured_peak()
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "peak_source": peak_kind,
+                "traffic": ncu_traffic(dom, w.name), "algorithmic_bytes_per_launch": int(algo[dom]),
+                "launch_ms": round(ms / launches, 4)}
+    kernels = {k: {"ms_total": round(v[0], 3), "launches": v[1]} for k, v in kern.items()}
+    gpu_launches = sum(v[1] for v in kern.values())
+
+    # end to end through the C ABI with host buffers (pinned): H2D of theta, D2H of results
+    e2e = None
+    th_h = torch.tensor(theta).pin_memory()
+    fit_h = torch.empty(n, dtype=torch.float64).pin_memory()
+    tc_h = torch.empty(n, dtype=torch.int64).pin_memory()
+    if not args.no_e2e:
+        for _ in range(max(1, args.warmup)):
+            fc.fcas_fitness(ctx, th_h, fit_h, tc_h, stream=stream.cuda_stream)
+        ranks.barrier()
+        torch.cuda.synchronize(dev)
+        h0 = time.perf_counter()
+        for _ in range(args.steps):
+            fc.fcas_fitness(ctx, th_h, fit_h, tc_h, stream=stream.cuda_stream)
+        torch.cuda.synchronize(dev)
+        e2e_s = time.perf_counter() - h0
+        ranks.barrier()
+        e2e_value, _ = aggregate(ranks, n * args.steps, e2e_s)
+        e2e = {"value": round(e2e_value, 2), "unit": UNIT, "h2d_bytes_per_step": int(th_h.numel() * 8),
+               "d2h_bytes_per_step": int(n * 16)}
+    ctx.close()
+
+    # plain binary64 form on the same workload (fewer steps: it is binary64-ALU bound)
+    fp64 = None
+    if args.fp64_steps > 0:
+        ctx64 = fc.fcas_create(data["det"], data["psd"], data["data"], w.n_fft, w.fs, w.f_low, w.f_high,
+                               precision="fp64", max_batch=args.max_batch)
+        for _ in range(1):
+            fc.fcas_fitness(ctx64, th, fit, tc, stream=stream.cuda_stream)
+        ranks.barrier()
+        torch.cuda.synchronize(dev)
+        t0.record(stream)
+        for _ in range(args.fp64_steps):
+            fc.fcas_fitness(ctx64, th, fit, tc, stream=stream.cuda_stream)
+        t1.record(stream)
+        torch.cuda.synchronize(dev)
+        s64 = t0.elapsed_time(t1) / 1e3
+        v64, _ = aggregate(ranks, n * args.fp64_steps, s64)
+        fp64 = {"value": round(v64, 2), "unit": UNIT, "steps": args.fp64_steps,
+                "ms_per_step": round(1e3 * s64 / args.fp64_steps, 3), "dtype": "f64"}
+        ctx64.close()
+
+    out = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": ranks.world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(1e3 * slowest / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "detectors": list(w.detectors), "n_fft": w.n_fft, "n_samples": w.n_samples,
+                   "fs": w.fs, "band_hz": [w.f_low, w.f_high], "particles_per_gpu": n,
+                   "precision": "fp32 + float-float phase", "chunk": info["chunk"],
+                   "l2": "inputs larger than L2 (intermediate %.1f GB per step), no flush" % (n * d * nn * 8 / 1e9)},
+        "roofline": roofline, "kernels": kernels, "gpu_launches": gpu_launches, "e2e": e2e, "clocks": clock,
+        "fp64_form": fp64,
+        "search_time_over_data_time": {"value": round(PSO_EVALS / value / DATA_SECONDS, 5),
+                                       "how": "extrapolated: 8 runs x 40 particles x 2000 iterations / value / 3600 s"},
+        "paper_context": {"search_over_data": [1.4, 0.5], "hardware": "1 KNL node per PSO run, FP64"},
+    }
+    if ranks.rank == 0 and args.cpu_sample > 0:
+        out["cpu_baseline"] = cpu_baseline(w, data, theta, args.cpu_sample)
+    return out
+
+
+def cpu_baseline(w, data, theta, sample):
+    from oracle import fcas_oracle as o
+    setup = o.OracleSetup(data["det"], data["psd"], data["data"], w.n_fft, w.fs, w.f_low, w.f_high)
+    t = time.perf_counter()
+    for th in theta[:sample]:
+        o.fitness(setup, th)
+    dt = time.perf_counter() - t
+    return {"value": round(sample / dt, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{sample} particles of the same workload, FP64 numpy oracle, one thread, data preparation excluded"}
+
+
+def bench_reference(args, ranks):
+    w = sd.workload_by_name(args.workload)
+    if ranks.rank != 0:          # under torchrun only rank 0 times the oracle; the others do no work
+        return None
+    from oracle import fcas_oracle as o
+    data, theta = workload_inputs(w, 0)
+    setup = o.OracleSetup(data["det"], data["psd"], data["data"], w.n_fft, w.fs, w.f_low, w.f_high)
+    per_step = 1
+    for j in range(args.warmup):
+        o.fitness(setup, theta[j % len(theta)])
+    t = time.perf_counter()
+    for j in range(args.steps):
+        o.fitness(setup, theta[j % len(theta)])
+    dt = time.perf_counter() - t
+    value = per_step * args.steps / dt
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ranks.world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * dt / args.steps, 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "n_fft": w.n_fft, "n_samples": w.n_samples,
+                       "particles_per_step": per_step},
+            "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "one particle of the workload per step, FP64 numpy oracle, one thread"},
+            "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        ranks = Ranks(backend="none")
+        out = bench_reference(args, ranks)
+    else:
+        ranks = Ranks()
+        out = bench_ours(args, ranks)
+    if ranks.rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+    if ranks.on:
+        ranks.dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,145 @@
+/*
+ * fcas.h -- C ABI of the GB300 coherent-fitness library (libfcas.so).
+ *
+ * The library evaluates the network GLRT coherent fitness of a fully-coherent all-sky search for
+ * compact-binary inspirals (Normandin & Mohanty, arXiv:2002.02150):
+ *
+ *   Gamma^2(Theta) = max over (t_c, A_1..A_4) of 2 lambda^(D),   Theta = (alpha, delta, tau0, tau1.5)
+ *
+ * (Sec. II.C, eq. gammaSqd, with the log-likelihood ratio of eq. loglikelihood and the inner
+ * product of eq. innprod), organised as in Sec. II.D: over-whitened data, precomputed template
+ * norms and the arrival delay moved onto the data (eq. data_template_innprod). The factor 2 makes
+ * a noiseless injection at the true parameters return its network SNR^2 (eq. optimalSNR).
+ *
+ * Conventions shared by every entry point
+ *  - Return value: FCAS_OK (0) on success, a negative FCAS_ERR_* code otherwise; the message of
+ *    the last failure on the calling thread is returned by fcas_last_error().
+ *  - Pointers marked "host or device" may point to host memory or to CUDA device memory; the
+ *    library tells them apart with cudaPointerGetAttributes. When every pointer argument of a
+ *    call is a device pointer the call is asynchronous on `stream`; when any is a host pointer the
+ *    call returns only after the results have been copied into it.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *  - The caller keeps ownership of every buffer it passes; the context owns everything it
+ *    allocates. A context must not be used from two threads at once.
+ *  - All floating-point inputs are IEEE binary64.
+ */
+#ifndef FCAS_H
+#define FCAS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FCAS_MAX_DET 8
+
+enum fcas_status {
+    FCAS_OK = 0,
+    FCAS_ERR_INVALID = -1,   /* bad size, NULL pointer, non-finite or out-of-range input */
+    FCAS_ERR_NOMEM = -2,     /* a device or host allocation failed */
+    FCAS_ERR_CUDA = -3,      /* a CUDA runtime call or kernel launch failed */
+    FCAS_ERR_TIMEOUT = -4,   /* a bounded device-side wait gave up (reserved) */
+    FCAS_ERR_STATE = -5      /* the context is not in a state that allows the call */
+};
+
+enum fcas_precision {
+    FCAS_PREC_FP64 = 0,      /* plain form: phase, products, FFTs and projection in binary64 */
+    FCAS_PREC_FP32 = 1       /* FP32 products/FFTs/projection; chirp and delay phase as
+                                float-float (hi + lo) values reduced mod 1 turn */
+};
+
+/* One interferometer: ECEF position and unit vectors along its two arms (Sec. II, eq. detresponse:
+ * the detector tensor is d = (x x^T - y y^T) / 2). */
+typedef struct fcas_detector {
+    double r[3];      /* ECEF position [m] */
+    double xarm[3];   /* unit vector along the x arm */
+    double yarm[3];   /* unit vector along the y arm */
+} fcas_detector;
+
+/* Data segment description. */
+typedef struct fcas_setup {
+    int32_t n_det;       /* D, 1..FCAS_MAX_DET */
+    int32_t precision;   /* enum fcas_precision */
+    int64_t n_samples;   /* samples per detector actually present, 1..n_fft */
+    int64_t n_fft;       /* FFT length N: a power of two, 16..2^24; samples n_samples..N-1 are zero */
+    double fs;           /* sampling rate [Hz] */
+    double f_low;        /* lower cutoff f_* [Hz] (> 0): the template is zero for f <= f_low (Sec. II.B) */
+    double f_high;       /* upper cutoff [Hz]: the template is zero for f > f_high (Sec. II.B) */
+    int32_t max_batch;   /* particles per internal chunk (0 = automatic); bounds scratch memory */
+    int32_t reserved;    /* must be 0 */
+} fcas_setup;
+
+typedef struct fcas_ctx fcas_ctx;
+
+/*
+ * fcas_create -- prepare a data segment (Sec. II.D).
+ *   setup : segment description (host).
+ *   det   : [n_det] detector geometry (host).
+ *   psd   : [n_det][n_fft/2+1] one-sided PSD S_n^i(f_k), f_k = k fs / n_fft (host or device).
+ *           Only bins with f_low < f_k <= f_high, 0 < k < n_fft/2 are read; they must be finite and > 0.
+ *   data  : [n_det][n_samples] real strain time series x^i (host or device).
+ * The segment is zero-padded to n_fft, transformed (x~[k] = dt sum_n x[n] e^{-2 pi i k n/N}),
+ * over-whitened (x~/S, Sec. II.D) and stored on the device together with the template norms
+ * <h_c|h_c>^i (Sec. II.D). The call is synchronous. On success *out receives a new context.
+ */
+int fcas_create(fcas_ctx** out, const fcas_setup* setup, const fcas_detector* det,
+                const double* psd, const double* data, void* stream);
+
+/*
+ * fcas_fitness -- coherent fitness of a batch of particles (Sec. II.C, eq. gammaSqd).
+ *   n       : number of particles (0 is a no-op).
+ *   theta   : [n][4] = (alpha [rad, ECEF azimuth], delta [rad, latitude in -pi/2..pi/2],
+ *             tau0 [s], tau1.5 [s]) (host or device). tau0 and tau1.5 must be > 0.
+ *   fitness : [n] Gamma^2 = max over t in [0, n_samples) of Gamma^2(t) (host or device).
+ *   tc      : [n] argmax sample index t (lowest index on ties); the coalescence time at the ECEF
+ *             origin is t / fs (host or device).
+ * A particle given on the device with a non-finite or non-positive chirp time gets fitness NaN
+ * and tc -1; given on the host the whole call fails with FCAS_ERR_INVALID instead.
+ */
+int fcas_fitness(fcas_ctx* ctx, int64_t n, const double* theta, double* fitness, int64_t* tc,
+                 void* stream);
+
+/* Release every resource held by the context (NULL is a no-op). Synchronises the device. */
+void fcas_destroy(fcas_ctx* ctx);
+
+/* Message of the last failure on the calling thread ("" if none). Valid until the next call. */
+const char* fcas_last_error(void);
+
+/* Library ABI version (major * 10000 + minor * 100 + patch). */
+int fcas_version(void);
+
+/* Layout and size facts of a context, for benchmarks and tests. */
+typedef struct fcas_info {
+    int64_t n_fft, n1, n2;      /* N = n1 * n2: pass A transforms length n2, pass B length n1 */
+    int64_t k_lo, k_hi;         /* first and last template bin */
+    int64_t n_band;             /* k_hi - k_lo + 1 */
+    int64_t chunk;              /* particles per internal chunk */
+    int32_t n_det, precision;
+    double scale;               /* power of two applied to the whitened data (Gamma^2 is invariant) */
+    double sigma2[FCAS_MAX_DET];/* unscaled template norms <h_c|h_c>^i */
+} fcas_info;
+
+int fcas_get_info(const fcas_ctx* ctx, fcas_info* info);
+
+/*
+ * Kernel timing: when enabled, every kernel launched by fcas_fitness is bracketed by CUDA events
+ * on the launching stream. fcas_profile_read synchronises those events and returns, for one
+ * kernel kind, the summed device time [ms] and the number of launches since the last enable.
+ */
+enum fcas_kernel_kind {
+    FCAS_KERNEL_GEOMETRY = 0,   /* per-particle sky geometry, chirp coefficients, G^-1 */
+    FCAS_KERNEL_PASS_A = 1,     /* fused template x data x delay phase + first FFT pass */
+    FCAS_KERNEL_PASS_B = 2,     /* second FFT pass + antenna projection + partial argmax */
+    FCAS_KERNEL_REDUCE = 3,     /* final argmax across CTAs */
+    FCAS_KERNEL_KINDS = 4
+};
+
+int fcas_profile_enable(fcas_ctx* ctx, int on);
+int fcas_profile_read(fcas_ctx* ctx, int kind, double* total_ms, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FCAS_H */

@@ -1,0 +1,484 @@
+// C ABI of libfcas: context lifetime, input validation, memory management and the launch
+// sequence of one fitness evaluation (geometry -> per chunk: pass A -> pass B -> reduce).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "fcas_kernels.cuh"
+
+using namespace fcas;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+#define FCAS_CUDA(call)                                                                              \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess) return fail(FCAS_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+struct EventPair {
+    cudaEvent_t a, b;
+    int kind;
+};
+
+}  // namespace
+
+struct fcas_ctx {
+    fcas_setup setup{};
+    int log_n = 0, log_n1 = 0, log_n2 = 0;
+    int64_t n1 = 0, n2 = 0;
+    int64_t k_lo = 0, k_hi = 0;
+    double df = 0.0, scale = 1.0;
+    double sigma2[FCAS_MAX_DET] = {};
+    double* d_det = nullptr;        // [D][9]
+    double* d_sigma2s = nullptr;    // scaled template norms
+    void* d_y = nullptr;            // Y (precision-dependent)
+    void* d_basis = nullptr;
+    void* d_tw = nullptr;           // precision-dependent copies of the twiddle tables
+    void* d_twlo = nullptr;
+    void* d_twhi = nullptr;
+    double2* d_tw64 = nullptr;      // binary64 tables (create path)
+    double2* d_twlo64 = nullptr;
+    double2* d_twhi64 = nullptr;
+    float2* d_tw32 = nullptr;
+    float2* d_twlo32 = nullptr;
+    float2* d_twhi32 = nullptr;
+    ParticleParams* d_params = nullptr;
+    int64_t params_cap = 0;
+    double* d_theta = nullptr;      // staging for host theta
+    double* d_fit = nullptr;        // staging for host outputs
+    int64_t* d_tc = nullptr;
+    int64_t stage_cap = 0;
+    void* d_inter = nullptr;        // [chunk][D][N2][N1] complex
+    Partial* d_partials = nullptr;  // [chunk][blocks per particle]
+    int64_t chunk = 0;
+    int64_t nb_partials = 0;
+    // profiling
+    bool prof = false;
+    std::vector<EventPair> events;
+    size_t events_used = 0;
+};
+
+namespace {
+
+void free_ctx(fcas_ctx* c) {
+    void* ptrs[] = {c->d_det, c->d_sigma2s, c->d_y, c->d_basis, c->d_tw64, c->d_twlo64, c->d_twhi64,
+                    c->d_tw32, c->d_twlo32, c->d_twhi32, c->d_params, c->d_theta, c->d_fit, c->d_tc,
+                    c->d_inter, c->d_partials};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    for (auto& e : c->events) {
+        cudaEventDestroy(e.a);
+        cudaEventDestroy(e.b);
+    }
+    delete c;
+}
+
+int ilog2_exact(int64_t v) {
+    if (v <= 0 || (v & (v - 1))) return -1;
+    int l = 0;
+    while ((int64_t(1) << l) < v) ++l;
+    return l;
+}
+
+template <typename T>
+int dev_alloc(T** p, size_t bytes, const char* what) {
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(FCAS_ERR_NOMEM, "cudaMalloc(%zu bytes) for %s failed: %s", bytes, what, cudaGetErrorString(e));
+    }
+    return FCAS_OK;
+}
+
+// Grow the per-particle buffers to hold n particles.
+int ensure_particles(fcas_ctx* c, int64_t n) {
+    if (n <= c->params_cap) return FCAS_OK;
+    if (c->d_params) cudaFree(c->d_params);
+    c->d_params = nullptr;
+    c->params_cap = 0;
+    int rc = dev_alloc(&c->d_params, sizeof(ParticleParams) * (size_t)n, "particle parameters");
+    if (rc) return rc;
+    c->params_cap = n;
+    return FCAS_OK;
+}
+
+int ensure_staging(fcas_ctx* c, int64_t n) {
+    if (n <= c->stage_cap) return FCAS_OK;
+    if (c->d_theta) cudaFree(c->d_theta);
+    if (c->d_fit) cudaFree(c->d_fit);
+    if (c->d_tc) cudaFree(c->d_tc);
+    c->d_theta = nullptr;
+    c->d_fit = nullptr;
+    c->d_tc = nullptr;
+    c->stage_cap = 0;
+    int rc = dev_alloc(&c->d_theta, sizeof(double) * 4 * (size_t)n, "theta staging");
+    if (!rc) rc = dev_alloc(&c->d_fit, sizeof(double) * (size_t)n, "fitness staging");
+    if (!rc) rc = dev_alloc(&c->d_tc, sizeof(int64_t) * (size_t)n, "tc staging");
+    if (rc) return rc;
+    c->stage_cap = n;
+    return FCAS_OK;
+}
+
+void prof_begin(fcas_ctx* c, int kind, cudaStream_t s, size_t* slot) {
+    *slot = SIZE_MAX;
+    if (!c->prof) return;
+    if (c->events_used == c->events.size()) {
+        if (c->events.size() >= 65536) return;
+        EventPair e;
+        if (cudaEventCreate(&e.a) != cudaSuccess || cudaEventCreate(&e.b) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+        c->events.push_back(e);
+    }
+    *slot = c->events_used++;
+    c->events[*slot].kind = kind;
+    cudaEventRecord(c->events[*slot].a, s);
+}
+
+void prof_end(fcas_ctx* c, size_t slot, cudaStream_t s) {
+    if (slot != SIZE_MAX) cudaEventRecord(c->events[slot].b, s);
+}
+
+FitnessPlan make_plan(const fcas_ctx* c) {
+    FitnessPlan p;
+    p.n_det = c->setup.n_det;
+    p.log_n = c->log_n;
+    p.log_n1 = c->log_n1;
+    p.log_n2 = c->log_n2;
+    p.n_samples = c->setup.n_samples;
+    const int log_tw = c->log_n1 > c->log_n2 ? c->log_n1 : c->log_n2;
+    p.tw_shift_a = log_tw - c->log_n2;
+    p.tw_shift_b = log_tw - c->log_n1;
+    p.y = c->d_y;
+    p.basis = c->d_basis;
+    p.tw = c->d_tw;
+    p.tw_lo = c->d_twlo;
+    p.tw_hi = c->d_twhi;
+    return p;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* fcas_last_error(void) { return g_last_error.c_str(); }
+
+int fcas_version(void) { return 100; }
+
+int fcas_create(fcas_ctx** out, const fcas_setup* setup, const fcas_detector* det, const double* psd,
+                const double* data, void* stream) {
+    g_last_error.clear();
+    if (!out || !setup || !det || !psd || !data) return fail(FCAS_ERR_INVALID, "fcas_create: NULL argument");
+    *out = nullptr;
+    const fcas_setup& s = *setup;
+    if (s.n_det < 1 || s.n_det > FCAS_MAX_DET)
+        return fail(FCAS_ERR_INVALID, "n_det = %d outside 1..%d", s.n_det, FCAS_MAX_DET);
+    if (s.precision != FCAS_PREC_FP32 && s.precision != FCAS_PREC_FP64)
+        return fail(FCAS_ERR_INVALID, "precision = %d is not FCAS_PREC_FP32 or FCAS_PREC_FP64", s.precision);
+    const int log_n = ilog2_exact(s.n_fft);
+    if (log_n < kMinLogN || log_n > kMaxLogN)
+        return fail(FCAS_ERR_INVALID, "n_fft = %lld is not a power of two in 2^%d..2^%d", (long long)s.n_fft, kMinLogN,
+                    kMaxLogN);
+    if (s.n_samples < 1 || s.n_samples > s.n_fft)
+        return fail(FCAS_ERR_INVALID, "n_samples = %lld outside 1..n_fft", (long long)s.n_samples);
+    if (!(std::isfinite(s.fs) && s.fs > 0.0)) return fail(FCAS_ERR_INVALID, "fs must be finite and > 0");
+    if (!(std::isfinite(s.f_low) && std::isfinite(s.f_high) && s.f_low > 0.0 && s.f_high > s.f_low))
+        return fail(FCAS_ERR_INVALID, "need 0 < f_low < f_high (finite)");
+    if (s.max_batch < 0 || s.reserved != 0) return fail(FCAS_ERR_INVALID, "max_batch < 0 or reserved != 0");
+    for (int i = 0; i < s.n_det; ++i) {
+        const double* v = det[i].r;
+        for (int q = 0; q < 9; ++q)
+            if (!std::isfinite(v[q])) return fail(FCAS_ERR_INVALID, "detector %d geometry is not finite", i);
+        const double nx = std::sqrt(det[i].xarm[0] * det[i].xarm[0] + det[i].xarm[1] * det[i].xarm[1] +
+                                    det[i].xarm[2] * det[i].xarm[2]);
+        const double ny = std::sqrt(det[i].yarm[0] * det[i].yarm[0] + det[i].yarm[1] * det[i].yarm[1] +
+                                    det[i].yarm[2] * det[i].yarm[2]);
+        if (std::fabs(nx - 1.0) > 1e-6 || std::fabs(ny - 1.0) > 1e-6)
+            return fail(FCAS_ERR_INVALID, "detector %d arm vectors are not unit vectors", i);
+    }
+    // band: f_low < k fs / N <= f_high, 0 < k < N/2
+    const int64_t n = s.n_fft;
+    int64_t k_lo = (int64_t)std::floor(s.f_low * (double)n / s.fs) + 1;
+    while (k_lo > 1 && (double)(k_lo - 1) * s.fs > s.f_low * (double)n) --k_lo;
+    while ((double)k_lo * s.fs <= s.f_low * (double)n) ++k_lo;
+    int64_t k_hi = (int64_t)std::floor(s.f_high * (double)n / s.fs);
+    while ((double)k_hi * s.fs > s.f_high * (double)n) --k_hi;
+    while ((double)(k_hi + 1) * s.fs <= s.f_high * (double)n) ++k_hi;
+    if (k_lo < 1) k_lo = 1;
+    if (k_hi > n / 2 - 1) k_hi = n / 2 - 1;
+    if (k_hi < k_lo) return fail(FCAS_ERR_INVALID, "the band (f_low, f_high] contains no frequency bin");
+
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    fcas_ctx* c = new fcas_ctx();
+    c->setup = s;
+    c->log_n = log_n;
+    c->log_n2 = log_n / 2;
+    c->log_n1 = log_n - c->log_n2;
+    c->n1 = (int64_t)1 << c->log_n1;
+    c->n2 = (int64_t)1 << c->log_n2;
+    c->k_lo = k_lo;
+    c->k_hi = k_hi;
+    c->df = s.fs / (double)n;
+    const int D = s.n_det;
+    const int64_t psd_row = n / 2 + 1;
+    double2* d_spec = nullptr;
+    double2* d_work = nullptr;
+    double* d_psd = nullptr;
+    double* d_data = nullptr;
+    int* d_flag = nullptr;
+    double* d_sig = nullptr;
+    const bool psd_dev = is_device_ptr(psd), data_dev = is_device_ptr(data);
+    auto cleanup = [&](int code) {
+        if (d_spec) cudaFree(d_spec);
+        if (d_work) cudaFree(d_work);
+        if (d_psd && !psd_dev) cudaFree(d_psd);
+        if (d_data && !data_dev) cudaFree(d_data);
+        if (d_flag) cudaFree(d_flag);
+        if (d_sig) cudaFree(d_sig);
+        if (code != FCAS_OK) free_ctx(c);
+        return code;
+    };
+#define FCAS_TRY(expr)                      \
+    do {                                    \
+        int rc_ = (expr);                   \
+        if (rc_ != FCAS_OK) return cleanup(rc_); \
+    } while (0)
+#define FCAS_TRYCUDA(call)                                                                                 \
+    do {                                                                                                   \
+        cudaError_t e_ = (call);                                                                           \
+        if (e_ != cudaSuccess) return cleanup(fail(FCAS_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_))); \
+    } while (0)
+
+    // inputs on the device
+    if (psd_dev) {
+        d_psd = const_cast<double*>(psd);
+    } else {
+        FCAS_TRY(dev_alloc(&d_psd, sizeof(double) * (size_t)D * psd_row, "psd"));
+        FCAS_TRYCUDA(cudaMemcpyAsync(d_psd, psd, sizeof(double) * (size_t)D * psd_row, cudaMemcpyHostToDevice, st));
+    }
+    if (data_dev) {
+        d_data = const_cast<double*>(data);
+    } else {
+        FCAS_TRY(dev_alloc(&d_data, sizeof(double) * (size_t)D * s.n_samples, "data"));
+        FCAS_TRYCUDA(cudaMemcpyAsync(d_data, data, sizeof(double) * (size_t)D * s.n_samples, cudaMemcpyHostToDevice,
+                                     st));
+    }
+    FCAS_TRY(dev_alloc(&d_flag, sizeof(int), "flag"));
+    FCAS_TRYCUDA(cudaMemsetAsync(d_flag, 0, sizeof(int), st));
+    FCAS_TRYCUDA(launch_check_finite(d_data, (int64_t)D * s.n_samples, d_flag, st));
+    FCAS_TRYCUDA(launch_check_psd(d_psd, D, psd_row, k_lo, k_hi, d_flag, st));
+    int h_flag = 0;
+    FCAS_TRYCUDA(cudaMemcpyAsync(&h_flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    FCAS_TRYCUDA(cudaStreamSynchronize(st));
+    if (h_flag & 1) return cleanup(fail(FCAS_ERR_INVALID, "data contains non-finite samples"));
+    if (h_flag & 2) return cleanup(fail(FCAS_ERR_INVALID, "psd is non-finite or <= 0 inside the band"));
+
+    // geometry table
+    FCAS_TRY(dev_alloc(&c->d_det, sizeof(double) * 9 * D, "detectors"));
+    FCAS_TRYCUDA(cudaMemcpyAsync(c->d_det, det, sizeof(double) * 9 * D, cudaMemcpyHostToDevice, st));
+
+    // template norms and the power-of-two scale that brings them near 1
+    FCAS_TRY(dev_alloc(&d_sig, sizeof(double) * D, "sigma2"));
+    FCAS_TRYCUDA(launch_sigma2(d_psd, D, psd_row, k_lo, k_hi, c->df, d_sig, st));
+    FCAS_TRYCUDA(cudaMemcpyAsync(c->sigma2, d_sig, sizeof(double) * D, cudaMemcpyDeviceToHost, st));
+    FCAS_TRYCUDA(cudaStreamSynchronize(st));
+    double smax = 0.0;
+    for (int i = 0; i < D; ++i) {
+        if (!(std::isfinite(c->sigma2[i]) && c->sigma2[i] > 0.0))
+            return cleanup(fail(FCAS_ERR_INVALID, "template norm of detector %d is not finite and positive", i));
+        smax = std::fmax(smax, c->sigma2[i]);
+    }
+    c->scale = std::ldexp(1.0, -(int)std::lround(0.5 * std::log2(smax)));
+    double s2s[FCAS_MAX_DET];
+    for (int i = 0; i < D; ++i) s2s[i] = c->sigma2[i] * c->scale * c->scale;
+    FCAS_TRY(dev_alloc(&c->d_sigma2s, sizeof(double) * D, "scaled sigma2"));
+    FCAS_TRYCUDA(cudaMemcpyAsync(c->d_sigma2s, s2s, sizeof(double) * D, cudaMemcpyHostToDevice, st));
+
+    // twiddle tables
+    const int log_tw = c->log_n1 > c->log_n2 ? c->log_n1 : c->log_n2;
+    const size_t ntw = (size_t)1 << log_tw;
+    const size_t nlo = (size_t)1 << kTwLoBits;
+    const size_t nhi = log_n > kTwLoBits ? ((size_t)1 << (log_n - kTwLoBits)) : 1;
+    FCAS_TRY(dev_alloc(&c->d_tw64, sizeof(double2) * ntw, "twiddles"));
+    FCAS_TRY(dev_alloc(&c->d_twlo64, sizeof(double2) * nlo, "twiddles"));
+    FCAS_TRY(dev_alloc(&c->d_twhi64, sizeof(double2) * nhi, "twiddles"));
+    FCAS_TRY(dev_alloc(&c->d_tw32, sizeof(float2) * ntw, "twiddles"));
+    FCAS_TRY(dev_alloc(&c->d_twlo32, sizeof(float2) * nlo, "twiddles"));
+    FCAS_TRY(dev_alloc(&c->d_twhi32, sizeof(float2) * nhi, "twiddles"));
+    FCAS_TRYCUDA(launch_tables(log_n, c->log_n1, c->log_n2, c->d_tw64, c->d_twlo64, c->d_twhi64, c->d_tw32,
+                               c->d_twlo32, c->d_twhi32, st));
+    const bool fp32 = s.precision == FCAS_PREC_FP32;
+    c->d_tw = fp32 ? (void*)c->d_tw32 : (void*)c->d_tw64;
+    c->d_twlo = fp32 ? (void*)c->d_twlo32 : (void*)c->d_twlo64;
+    c->d_twhi = fp32 ? (void*)c->d_twhi32 : (void*)c->d_twhi64;
+
+    // forward FFT of the data (binary64) and the whitened, re-laid-out band spectrum
+    FCAS_TRY(dev_alloc(&d_spec, sizeof(double2) * (size_t)D * n, "data spectrum"));
+    FCAS_TRY(dev_alloc(&d_work, sizeof(double2) * (size_t)D * n, "data FFT work"));
+    FCAS_TRYCUDA(launch_data_fft(d_data, D, s.n_samples, log_n, c->log_n1, c->log_n2, c->d_tw64, log_tw - c->log_n2,
+                                 log_tw - c->log_n1, c->d_twlo64, c->d_twhi64, d_work, d_spec, st));
+    const size_t half = (size_t)(n / 2);
+    const size_t ysz = (fp32 ? sizeof(float2) : sizeof(double2)) * (size_t)D * half;
+    const size_t bsz = (fp32 ? sizeof(BasisF) : sizeof(BasisD)) * half;
+    FCAS_TRY(dev_alloc(&c->d_y, ysz, "whitened spectrum"));
+    FCAS_TRY(dev_alloc(&c->d_basis, bsz, "chirp basis"));
+    FCAS_TRYCUDA(launch_prep(d_spec, d_psd, D, psd_row, log_n, c->log_n1, c->log_n2, k_lo, k_hi, s.fs, s.f_low,
+                             c->scale, s.precision, c->d_y, c->d_basis, st));
+
+    // scratch for the fitness path
+    const size_t csz = fp32 ? sizeof(float2) : sizeof(double2);
+    const size_t per_particle = csz * (size_t)D * n;
+    int64_t chunk = s.max_batch;
+    if (chunk == 0) {
+        const size_t budget = (size_t)16 << 30;
+        chunk = (int64_t)(budget / per_particle);
+        if (chunk > 64) chunk = 64;
+        if (chunk < 1) chunk = 1;
+    }
+    c->chunk = chunk;
+    c->nb_partials = pass_b_blocks_per_particle(c->log_n1, c->log_n2);
+    FCAS_TRY(dev_alloc(&c->d_inter, per_particle * (size_t)chunk, "intermediate transform"));
+    FCAS_TRY(dev_alloc(&c->d_partials, sizeof(Partial) * (size_t)chunk * c->nb_partials, "argmax partials"));
+    FCAS_TRYCUDA(cudaStreamSynchronize(st));
+#undef FCAS_TRY
+#undef FCAS_TRYCUDA
+    cleanup(FCAS_OK);
+    *out = c;
+    return FCAS_OK;
+}
+
+int fcas_fitness(fcas_ctx* c, int64_t n, const double* theta, double* fitness, int64_t* tc, void* stream) {
+    g_last_error.clear();
+    if (!c) return fail(FCAS_ERR_INVALID, "fcas_fitness: NULL context");
+    if (n < 0) return fail(FCAS_ERR_INVALID, "fcas_fitness: n < 0");
+    if (n == 0) return FCAS_OK;
+    if (!theta || !fitness || !tc) return fail(FCAS_ERR_INVALID, "fcas_fitness: NULL array");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool th_dev = is_device_ptr(theta), f_dev = is_device_ptr(fitness), t_dev = is_device_ptr(tc);
+    if (!th_dev) {
+        for (int64_t p = 0; p < n; ++p) {
+            const double* t = theta + 4 * p;
+            if (!(std::isfinite(t[0]) && std::isfinite(t[1]) && std::isfinite(t[2]) && std::isfinite(t[3]) &&
+                  t[2] > 0.0 && t[3] > 0.0))
+                return fail(FCAS_ERR_INVALID, "particle %lld: non-finite angle or non-positive chirp time",
+                            (long long)p);
+        }
+    }
+    int rc = ensure_particles(c, n);
+    if (rc) return rc;
+    if (!th_dev || !f_dev || !t_dev) {
+        rc = ensure_staging(c, n);
+        if (rc) return rc;
+    }
+    const double* d_theta = theta;
+    if (!th_dev) {
+        FCAS_CUDA(cudaMemcpyAsync(c->d_theta, theta, sizeof(double) * 4 * (size_t)n, cudaMemcpyHostToDevice, st));
+        d_theta = c->d_theta;
+    }
+    double* d_fit = f_dev ? fitness : c->d_fit;
+    int64_t* d_tc = t_dev ? tc : c->d_tc;
+    size_t slot;
+    prof_begin(c, FCAS_KERNEL_GEOMETRY, st, &slot);
+    FCAS_CUDA(launch_geometry(d_theta, n, c->d_params, c->d_det, c->d_sigma2s, c->setup.n_det, c->setup.f_low, c->df,
+                              st));
+    prof_end(c, slot, st);
+    const FitnessPlan plan = make_plan(c);
+    const bool fp32 = c->setup.precision == FCAS_PREC_FP32;
+    for (int64_t p0 = 0; p0 < n; p0 += c->chunk) {
+        const int64_t np = (n - p0) < c->chunk ? (n - p0) : c->chunk;
+        prof_begin(c, FCAS_KERNEL_PASS_A, st, &slot);
+        FCAS_CUDA(fp32 ? launch_pass_a<float>(plan, c->d_params, p0, np, c->d_inter, st)
+                       : launch_pass_a<double>(plan, c->d_params, p0, np, c->d_inter, st));
+        prof_end(c, slot, st);
+        prof_begin(c, FCAS_KERNEL_PASS_B, st, &slot);
+        FCAS_CUDA(fp32 ? launch_pass_b<float>(plan, c->d_params, p0, np, c->d_inter, c->d_partials, st)
+                       : launch_pass_b<double>(plan, c->d_params, p0, np, c->d_inter, c->d_partials, st));
+        prof_end(c, slot, st);
+        prof_begin(c, FCAS_KERNEL_REDUCE, st, &slot);
+        FCAS_CUDA(launch_reduce(c->d_partials, c->nb_partials, c->d_params, p0, np, d_fit, d_tc, st));
+        prof_end(c, slot, st);
+    }
+    if (!f_dev) FCAS_CUDA(cudaMemcpyAsync(fitness, d_fit, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, st));
+    if (!t_dev) FCAS_CUDA(cudaMemcpyAsync(tc, d_tc, sizeof(int64_t) * (size_t)n, cudaMemcpyDeviceToHost, st));
+    if (!th_dev || !f_dev || !t_dev) FCAS_CUDA(cudaStreamSynchronize(st));
+    return FCAS_OK;
+}
+
+void fcas_destroy(fcas_ctx* c) {
+    if (!c) return;
+    cudaDeviceSynchronize();
+    free_ctx(c);
+}
+
+int fcas_get_info(const fcas_ctx* c, fcas_info* info) {
+    if (!c || !info) return fail(FCAS_ERR_INVALID, "fcas_get_info: NULL argument");
+    std::memset(info, 0, sizeof(*info));
+    info->n_fft = c->setup.n_fft;
+    info->n1 = c->n1;
+    info->n2 = c->n2;
+    info->k_lo = c->k_lo;
+    info->k_hi = c->k_hi;
+    info->n_band = c->k_hi - c->k_lo + 1;
+    info->chunk = c->chunk;
+    info->n_det = c->setup.n_det;
+    info->precision = c->setup.precision;
+    info->scale = c->scale;
+    for (int i = 0; i < c->setup.n_det; ++i) info->sigma2[i] = c->sigma2[i];
+    return FCAS_OK;
+}
+
+int fcas_profile_enable(fcas_ctx* c, int on) {
+    if (!c) return fail(FCAS_ERR_INVALID, "fcas_profile_enable: NULL context");
+    c->prof = on != 0;
+    c->events_used = 0;
+    return FCAS_OK;
+}
+
+int fcas_profile_read(fcas_ctx* c, int kind, double* total_ms, int64_t* launches) {
+    if (!c || !total_ms || !launches) return fail(FCAS_ERR_INVALID, "fcas_profile_read: NULL argument");
+    if (kind < 0 || kind >= FCAS_KERNEL_KINDS) return fail(FCAS_ERR_INVALID, "unknown kernel kind %d", kind);
+    double sum = 0.0;
+    int64_t cnt = 0;
+    for (size_t i = 0; i < c->events_used; ++i) {
+        if (c->events[i].kind != kind) continue;
+        FCAS_CUDA(cudaEventSynchronize(c->events[i].b));
+        float ms = 0.f;
+        FCAS_CUDA(cudaEventElapsedTime(&ms, c->events[i].a, c->events[i].b));
+        sum += ms;
+        ++cnt;
+    }
+    *total_ms = sum;
+    *launches = cnt;
+    return FCAS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,75 @@
+// Kernel launchers of the fitness path (defined in fcas_kernels.cu) and of the create path
+// (fcas_create.cu).
+#pragma once
+
+#include "fcas_internal.cuh"
+
+namespace fcas {
+
+// Float-float chirp-phase basis phi^-5/3, phi^-1, phi^-2/3, phi^-1/3 of one bin (hi, lo pairs).
+struct __align__(16) BasisF {
+    float4 a;   // (b53 hi, b53 lo, b1 hi, b1 lo)
+    float4 b;   // (b23 hi, b23 lo, b13 hi, b13 lo)
+};
+struct __align__(16) BasisD {
+    double2 a;  // (b53, b1)
+    double2 b;  // (b23, b13)
+};
+template <typename R> struct basis_of;
+template <> struct basis_of<float> { using type = BasisF; };
+template <> struct basis_of<double> { using type = BasisD; };
+template <typename R> using Basis = typename basis_of<R>::type;
+
+struct Partial {
+    double val;
+    int64_t t;
+};
+
+struct FitnessPlan {
+    int n_det;
+    int log_n, log_n1, log_n2;
+    int64_t n_samples;
+    int tw_shift_a, tw_shift_b;   // log2(table length / transform length)
+    const void* y;                // Y layout [i][k1 / K1B][k2 < N2/2][k1 % K1B]
+    const void* basis;            // basis layout [k1 / K1B][k2 < N2/2][k1 % K1B]
+    const void* tw;               // e^{2 pi i m / TWL}, TWL = max(N1, N2)
+    const void* tw_lo;            // e^{2 pi i m / N}, m < 4096
+    const void* tw_hi;            // e^{2 pi i 4096 m / N}, m < max(1, N / 4096)
+};
+
+// Per-particle geometry (binary64): chirp coefficients, delays, antenna patterns, G^-1.
+cudaError_t launch_geometry(const double* theta, int64_t n, ParticleParams* out, const double* det9,
+                            const double* sigma2_scaled, int n_det, double f_star, double df,
+                            cudaStream_t s);
+
+// Pass A for particles [p0, p0 + np): writes the intermediate [np][D][N2][N1].
+template <typename Real>
+cudaError_t launch_pass_a(const FitnessPlan& plan, const ParticleParams* params, int64_t p0, int64_t np,
+                          void* inter, cudaStream_t s);
+// Pass B + projection + partial argmax: writes partials [np][N2 / TB].
+template <typename Real>
+cudaError_t launch_pass_b(const FitnessPlan& plan, const ParticleParams* params, int64_t p0, int64_t np,
+                          const void* inter, Partial* partials, cudaStream_t s);
+// Final argmax: fitness[p0 + p], tc[p0 + p].
+cudaError_t launch_reduce(const Partial* partials, int64_t nb, const ParticleParams* params, int64_t p0,
+                          int64_t np, double* fitness, int64_t* tc, cudaStream_t s);
+
+int pass_b_blocks_per_particle(int log_n1, int log_n2);
+int pass_a_k1b_for(int log_n2);
+
+// ---- create path (fcas_create.cu) ----
+cudaError_t launch_tables(int log_n, int log_n1, int log_n2, double2* tw64, double2* twlo64, double2* twhi64,
+                          float2* tw32, float2* twlo32, float2* twhi32, cudaStream_t s);
+cudaError_t launch_check_finite(const double* x, int64_t n, int* flag, cudaStream_t s);
+cudaError_t launch_check_psd(const double* psd, int n_det, int64_t row, int64_t k_lo, int64_t k_hi, int* flag,
+                             cudaStream_t s);
+cudaError_t launch_sigma2(const double* psd, int n_det, int64_t row, int64_t k_lo, int64_t k_hi, double df,
+                          double* sigma2, cudaStream_t s);
+cudaError_t launch_data_fft(const double* data, int n_det, int64_t n_samples, int log_n, int log_n1, int log_n2,
+                            const double2* tw64, int tw_shift_a, int tw_shift_b, const double2* twlo64,
+                            const double2* twhi64, double2* work, double2* spec, cudaStream_t s);
+cudaError_t launch_prep(const double2* spec, const double* psd, int n_det, int64_t psd_row, int log_n, int log_n1,
+                        int log_n2, int64_t k_lo, int64_t k_hi, double fs, double f_star, double scale,
+                        int precision, void* y, void* basis, cudaStream_t s);
+
+}  // namespace fcas

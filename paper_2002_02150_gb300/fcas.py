@@ -1,0 +1,203 @@
+"""Python binding of libfcas (argument marshalling only; every computation runs in the library).
+
+Functions carry the C names: ``fcas_create``, ``fcas_fitness``, ``fcas_destroy``,
+``fcas_last_error``, ``fcas_get_info``, ``fcas_profile_enable``, ``fcas_profile_read``.
+Arrays may be numpy arrays (host memory) or torch CUDA tensors (device memory); device arrays make
+the call asynchronous on the given stream (default: torch's current stream).
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfcas.so")
+
+FCAS_MAX_DET = 8
+FCAS_PREC_FP64 = 0
+FCAS_PREC_FP32 = 1
+KERNEL_KINDS = {"geometry": 0, "pass_a": 1, "pass_b": 2, "reduce": 3}
+
+
+class FcasError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libfcas error {code}: {msg}")
+        self.code = code
+
+
+class fcas_detector(ctypes.Structure):
+    _fields_ = [("r", ctypes.c_double * 3), ("xarm", ctypes.c_double * 3), ("yarm", ctypes.c_double * 3)]
+
+
+class fcas_setup(ctypes.Structure):
+    _fields_ = [("n_det", ctypes.c_int32), ("precision", ctypes.c_int32), ("n_samples", ctypes.c_int64),
+                ("n_fft", ctypes.c_int64), ("fs", ctypes.c_double), ("f_low", ctypes.c_double),
+                ("f_high", ctypes.c_double), ("max_batch", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class fcas_info(ctypes.Structure):
+    _fields_ = [("n_fft", ctypes.c_int64), ("n1", ctypes.c_int64), ("n2", ctypes.c_int64),
+                ("k_lo", ctypes.c_int64), ("k_hi", ctypes.c_int64), ("n_band", ctypes.c_int64),
+                ("chunk", ctypes.c_int64), ("n_det", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("scale", ctypes.c_double), ("sigma2", ctypes.c_double * FCAS_MAX_DET)]
+
+
+_lib = None
+
+
+def load_library():
+    """Load libfcas.so; raise if it has not been built (there is no fallback implementation)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build the CUDA library first "
+                          "(python -c 'import __graft_entry__ as g; g.build()')")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i64, i32, dp = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    lib.fcas_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(fcas_setup), ctypes.POINTER(fcas_detector),
+                                vp, vp, vp]
+    lib.fcas_create.restype = i32
+    lib.fcas_fitness.argtypes = [vp, i64, vp, vp, vp, vp]
+    lib.fcas_fitness.restype = i32
+    lib.fcas_destroy.argtypes = [vp]
+    lib.fcas_destroy.restype = None
+    lib.fcas_last_error.argtypes = []
+    lib.fcas_last_error.restype = ctypes.c_char_p
+    lib.fcas_version.argtypes = []
+    lib.fcas_version.restype = i32
+    lib.fcas_get_info.argtypes = [vp, ctypes.POINTER(fcas_info)]
+    lib.fcas_get_info.restype = i32
+    lib.fcas_profile_enable.argtypes = [vp, i32]
+    lib.fcas_profile_enable.restype = i32
+    lib.fcas_profile_read.argtypes = [vp, i32, ctypes.POINTER(dp), ctypes.POINTER(i64)]
+    lib.fcas_profile_read.restype = i32
+    _lib = lib
+    return lib
+
+
+def fcas_last_error():
+    return load_library().fcas_last_error().decode()
+
+
+def _check(rc):
+    if rc != 0:
+        raise FcasError(rc, fcas_last_error())
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x, dtype):
+    """Pointer to a contiguous array of the given numpy dtype (host numpy or device torch tensor).
+    Returns (pointer, keep-alive object)."""
+    if _is_torch(x):
+        import torch
+        want = {np.float64: torch.float64, np.int64: torch.int64}[dtype]
+        if x.dtype != want or not x.is_contiguous():
+            x = x.to(want).contiguous()
+        return ctypes.c_void_p(x.data_ptr()), x
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return ctypes.c_void_p(a.ctypes.data), a
+
+
+def _stream(stream, *arrays):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    if any(_is_torch(a) and a.is_cuda for a in arrays if a is not None):
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return ctypes.c_void_p(0)
+
+
+class Context:
+    """Owns one fcas_ctx (a prepared data segment)."""
+
+    def __init__(self, handle, setup):
+        self.handle = handle
+        self.setup = setup
+
+    def close(self):
+        if self.handle:
+            load_library().fcas_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def fcas_create(det, psd, data, n_fft, fs, f_low, f_high, precision="fp32", max_batch=0, stream=None):
+    """Prepare a data segment. det: (D, 9) ECEF r, x arm, y arm; psd: (D, n_fft/2+1); data: (D, n_samples)."""
+    lib = load_library()
+    det = np.asarray(det, dtype=np.float64).reshape(-1, 9)
+    n_det = det.shape[0]
+    dets = (fcas_detector * n_det)()
+    for i in range(n_det):
+        dets[i].r[:] = det[i, 0:3]
+        dets[i].xarm[:] = det[i, 3:6]
+        dets[i].yarm[:] = det[i, 6:9]
+    n_samples = int(data.shape[-1])
+    prec = {"fp32": FCAS_PREC_FP32, "fp64": FCAS_PREC_FP64}[precision] if isinstance(precision, str) else int(precision)
+    setup = fcas_setup(n_det, prec, n_samples, int(n_fft), float(fs), float(f_low), float(f_high), int(max_batch), 0)
+    p_psd, k1 = _ptr(psd, np.float64)
+    p_data, k2 = _ptr(data, np.float64)
+    handle = ctypes.c_void_p()
+    _check(lib.fcas_create(ctypes.byref(handle), ctypes.byref(setup), dets, p_psd, p_data, _stream(stream, psd, data)))
+    return Context(handle, setup)
+
+
+def fcas_fitness(ctx, theta, fitness=None, tc=None, stream=None):
+    """Gamma^2 and argmax t_c of a batch of particles theta (n, 4) = (alpha, delta, tau0, tau1.5).
+    Outputs default to the memory kind of theta (numpy on host, torch on its CUDA device)."""
+    lib = load_library()
+    n = int(theta.shape[0]) if len(theta.shape) == 2 else int(np.prod(theta.shape)) // 4
+    if fitness is None or tc is None:
+        if _is_torch(theta) and theta.is_cuda:
+            import torch
+            fitness = torch.empty(n, dtype=torch.float64, device=theta.device) if fitness is None else fitness
+            tc = torch.empty(n, dtype=torch.int64, device=theta.device) if tc is None else tc
+        else:
+            fitness = np.empty(n, dtype=np.float64) if fitness is None else fitness
+            tc = np.empty(n, dtype=np.int64) if tc is None else tc
+    p_th, k1 = _ptr(theta, np.float64)
+    p_f, k2 = _ptr(fitness, np.float64)
+    p_t, k3 = _ptr(tc, np.int64)
+    _check(lib.fcas_fitness(ctx.handle, n, p_th, p_f, p_t, _stream(stream, theta, fitness, tc)))
+    if k2 is not fitness and _is_torch(fitness):
+        fitness.copy_(k2)
+    if k3 is not tc and _is_torch(tc):
+        tc.copy_(k3)
+    return (k2 if not _is_torch(fitness) else fitness), (k3 if not _is_torch(tc) else tc)
+
+
+def fcas_destroy(ctx):
+    ctx.close()
+
+
+def fcas_get_info(ctx):
+    info = fcas_info()
+    _check(load_library().fcas_get_info(ctx.handle, ctypes.byref(info)))
+    return {f: (list(getattr(info, f)) if f == "sigma2" else getattr(info, f)) for f, _ in fcas_info._fields_}
+
+
+def fcas_profile_enable(ctx, on=True):
+    _check(load_library().fcas_profile_enable(ctx.handle, 1 if on else 0))
+
+
+def fcas_profile_read(ctx, kind):
+    total = ctypes.c_double()
+    launches = ctypes.c_int64()
+    k = KERNEL_KINDS[kind] if isinstance(kind, str) else int(kind)
+    _check(load_library().fcas_profile_read(ctx.handle, k, ctypes.byref(total), ctypes.byref(launches)))
+    return total.value, launches.value

@@ -1,0 +1,174 @@
+"""GPU parity of the coherent fitness (through the C ABI) against the FP64 oracle."""
+
+import dataclasses
+import math
+
+import numpy as np
+import pytest
+
+import synthdata as sd
+from oracle import fcas_oracle as o
+from parity_util import RTOL, assert_parity, gpu_fitness, make_ctx, oracle_setup
+
+pytestmark = pytest.mark.gpu
+
+FORMS = ["fp32", "fp64"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2002_02150_gb300 import build as b
+    b.build()
+
+
+@pytest.mark.parametrize("precision", FORMS)
+def test_small_workload_matches_oracle(precision):
+    w = sd.SMALL
+    data = sd.make_dataset(w, 0)
+    theta = sd.make_particles(w, seed=0)
+    with make_ctx(w, data, precision) as ctx:
+        fit, tc = gpu_fitness(ctx, theta)
+    assert_parity(oracle_setup(w, data), theta, fit, tc, precision, "SMALL")
+
+
+# transform lengths from 2^4 to 2^14 (odd and even log2, every pass shape), ragged sample counts
+SIZES = [(16, 16, 16.0, 1.5, 6.0), (32, 27, 32.0, 2.2, 12.0), (64, 50, 64.0, 5.0, 28.0),
+         (128, 128, 128.0, 10.0, 50.0), (256, 200, 128.0, 12.0, 60.0), (512, 511, 256.0, 30.0, 120.0),
+         (2048, 1500, 512.0, 60.0, 250.0), (8192, 8000, 512.0, 40.0, 200.0), (16384, 12345, 1024.0, 80.0, 400.0)]
+
+
+@pytest.mark.parametrize("precision", FORMS)
+@pytest.mark.parametrize("n_fft,n_samples,fs,f_low,f_high", SIZES)
+def test_sizes_and_ragged_lengths(precision, n_fft, n_samples, fs, f_low, f_high):
+    w = dataclasses.replace(sd.SMALL, n_fft=n_fft, n_samples=n_samples, fs=fs, f_low=f_low, f_high=f_high,
+                            arrival_s=0.3 * n_samples / fs)
+    data = sd.make_dataset(w, 3)
+    theta = sd.make_particles(w, 9, seed=3, f_star=f_low)
+    with make_ctx(w, data, precision) as ctx:
+        fit, tc = gpu_fitness(ctx, theta)
+    assert_parity(oracle_setup(w, data), theta, fit, tc, precision, f"N={n_fft}")
+
+
+@pytest.mark.parametrize("precision", FORMS)
+def test_noiseless_injection_gives_snr_squared(precision):
+    w = dataclasses.replace(sd.SMALL, n_samples=sd.SMALL.n_fft)
+    data = sd.make_dataset(w, 2, noise=False)
+    inj = data["inj"]
+    t0, _, t15, _ = o.chirp_times_from_masses(inj["m1"], inj["m2"], w.f_low)
+    with make_ctx(w, data, precision) as ctx:
+        fit, tc = gpu_fitness(ctx, [[inj["alpha"], inj["delta"], t0, t15]])
+    assert fit[0] == pytest.approx(inj["snr"] ** 2, rel=RTOL[precision])
+    assert tc[0] == round(inj["t_c"] * w.fs)
+
+
+@pytest.mark.parametrize("precision", FORMS)
+@pytest.mark.parametrize("dets", [("L1",), ("H1", "V1"), ("H1", "L1", "V1"), ("H1", "L1", "V1", "K1", "H1")])
+def test_network_sizes(precision, dets):
+    w = dataclasses.replace(sd.SMALL, detectors=dets)
+    data = sd.make_dataset(w, 5)
+    theta = sd.make_particles(w, 6, seed=5)
+    with make_ctx(w, data, precision) as ctx:
+        fit, tc = gpu_fitness(ctx, theta)
+    assert_parity(oracle_setup(w, data), theta, fit, tc, precision, f"D={len(dets)}")
+
+
+@pytest.mark.parametrize("precision", FORMS)
+def test_config1_full_batch(precision):
+    w = sd.C1
+    data = sd.make_dataset(w, 0)
+    theta = sd.make_particles(w, seed=0)
+    with make_ctx(w, data, precision) as ctx:
+        fit, tc = gpu_fitness(ctx, theta)
+    assert_parity(oracle_setup(w, data), theta, fit, tc, precision, "C1")
+
+
+def test_chunking_and_batch_edges():
+    import torch
+    import paper_2002_02150_gb300 as fc
+    w = sd.SMALL
+    data = sd.make_dataset(w, 1)
+    theta = sd.make_particles(w, 23, seed=1)
+    with make_ctx(w, data, "fp32") as ref_ctx, make_ctx(w, data, "fp32", max_batch=5) as ctx:
+        ref_f, ref_t = gpu_fitness(ref_ctx, theta)
+        f, t = gpu_fitness(ctx, theta)
+        np.testing.assert_array_equal(f, ref_f)
+        np.testing.assert_array_equal(t, ref_t)
+        one_f, one_t = gpu_fitness(ctx, theta[7:8])
+        assert one_f[0] == ref_f[7] and one_t[0] == ref_t[7]
+        # n = 0 is a no-op
+        e = torch.empty((0, 4), dtype=torch.float64, device="cuda:0")
+        f0, t0 = fc.fcas_fitness(ctx, e)
+        assert f0.numel() == 0
+        # host arrays in and out give the same numbers as device arrays
+        hf, ht = fc.fcas_fitness(ctx, theta)
+        np.testing.assert_array_equal(hf, ref_f)
+        np.testing.assert_array_equal(ht, ref_t)
+
+
+def test_invalid_particles():
+    import torch
+    import paper_2002_02150_gb300 as fc
+    w = sd.SMALL
+    data = sd.make_dataset(w, 1)
+    theta = sd.make_particles(w, 4, seed=1)
+    bad = theta.copy()
+    bad[1, 2] = -1.0
+    bad[2, 0] = math.nan
+    with make_ctx(w, data, "fp32") as ctx:
+        f, t = gpu_fitness(ctx, bad)
+        assert np.isnan(f[1]) and t[1] == -1 and np.isnan(f[2]) and t[2] == -1
+        ok_f, ok_t = gpu_fitness(ctx, theta[[0, 3]])
+        assert f[0] == ok_f[0] and f[3] == ok_f[1]
+        with pytest.raises(fc.FcasError):
+            fc.fcas_fitness(ctx, bad)
+
+
+def test_create_rejects_non_finite_inputs():
+    import paper_2002_02150_gb300 as fc
+    w = sd.SMALL
+    data = sd.make_dataset(w, 1)
+    d = data["data"].copy()
+    d[2, 17] = math.inf
+    with pytest.raises(fc.FcasError, match="non-finite"):
+        fc.fcas_create(data["det"], data["psd"], d, w.n_fft, w.fs, w.f_low, w.f_high)
+    p = data["psd"].copy()
+    p[0, 700] = 0.0          # inside the band (640, 2000] of this workload
+    with pytest.raises(fc.FcasError, match="psd"):
+        fc.fcas_create(data["det"], p, data["data"], w.n_fft, w.fs, w.f_low, w.f_high)
+
+
+def test_profiling_counts_launches():
+    import paper_2002_02150_gb300 as fc
+    w = sd.SMALL
+    data = sd.make_dataset(w, 1)
+    theta = sd.make_particles(w, 10, seed=1)
+    with make_ctx(w, data, "fp32", max_batch=4) as ctx:
+        fc.fcas_profile_enable(ctx, True)
+        gpu_fitness(ctx, theta)
+        ms, n = fc.fcas_profile_read(ctx, "pass_a")
+        assert n == 3 and ms > 0
+        assert fc.fcas_profile_read(ctx, "geometry")[1] == 1
+        info = fc.fcas_get_info(ctx)
+        assert info["n1"] * info["n2"] == w.n_fft and info["chunk"] == 4
+
+
+def test_config2_full_size_sampled():
+    """The 60-min workload in the launch configuration the benchmark times (320 particles, default
+    chunking): every particle has a finite, non-negative fitness and an in-range tc; sampled
+    particles match the oracle one by one in both forms."""
+    w = sd.C2
+    data = sd.make_dataset(w, 0)
+    theta = sd.make_particles(w, seed=0)
+    sample = [0, 157, 319]
+    setup = oracle_setup(w, data)
+    for precision in FORMS:
+        with make_ctx(w, data, precision) as ctx:
+            fit, tc = gpu_fitness(ctx, theta if precision == "fp32" else theta[sample])
+        if precision == "fp32":
+            assert np.all(np.isfinite(fit)) and np.all(fit >= 0)
+            assert np.all((tc >= 0) & (tc < w.n_samples))
+            fit, tc = fit[sample], tc[sample]
+        assert_parity(setup, theta[sample], fit, tc, precision, f"C2 {precision}")
