@@ -100,6 +100,40 @@ int fcas_create(fcas_ctx** out, const fcas_setup* setup, const fcas_detector* de
 int fcas_fitness(fcas_ctx* ctx, int64_t n, const double* theta, double* fitness, int64_t* tc,
                  void* stream);
 
+/*
+ * fcas_fitness_noalloc -- the same evaluation as fcas_fitness, for callers that cannot allocate
+ * device memory while they run. (The paper has no counterpart: this entry point exists for how the
+ * library is deployed, not for the method.)
+ *
+ * Who needs it: programs whose device memory is handed out by another runtime's pool and that may
+ * not call cudaMalloc themselves, and analysis loops that fix their memory footprint at start-up
+ * because an allocation that fails or stalls in mid-run would lose data. Such a caller creates the
+ * context during its set-up phase (fcas_create allocates) and evaluates particles with this call.
+ * fcas_fitness may allocate on a call (its particle buffers grow with the batch, host arrays
+ * are staged); this call allocates nothing: it calls no cudaMalloc, cudaFree or other allocating
+ * routine.
+ *
+ * Its scratch (per-particle parameters, the intermediate transform between the two FFT passes and
+ * the argmax partials) lives in one static device array of 32 MiB inside libfcas.so, which every
+ * GPU that loads the library holds until the process exits. One particle needs
+ * n_det * n_fft * (8 bytes FP32, 16 bytes FP64) plus ~0.3 KB; particles are processed in chunks
+ * that fit. A context whose single particle does not fit (e.g. 4 detectors at n_fft >= 2^20 in
+ * FP32) is rejected with FCAS_ERR_INVALID and a message naming the sizes.
+ *
+ *   ctx, n, theta, fitness, tc : as for fcas_fitness, except that theta, fitness and tc must be
+ *                                device pointers (host arrays would need staging memory):
+ *                                FCAS_ERR_INVALID otherwise.
+ *   stream                     : as for fcas_fitness; the call is asynchronous on it.
+ *
+ * The first call on a device looks up the device address of the scratch array (once per device,
+ * with that device current); make that first call before any stream capture. Every call, from every
+ * context and thread, shares the one array and leaves its contents behind; nothing in it needs to
+ * start at zero because each call writes every word it reads. Calls that overlap on the GPU
+ * (different streams, or different host threads) race on the array: serialise them.
+ */
+int fcas_fitness_noalloc(const fcas_ctx* ctx, int64_t n, const double* theta, double* fitness, int64_t* tc,
+                         void* stream);
+
 /* Release every resource held by the context (NULL is a no-op). Synchronises the device. */
 void fcas_destroy(fcas_ctx* ctx);
 

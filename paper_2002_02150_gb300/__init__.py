@@ -1,8 +1,8 @@
 """GB300 coherent-fitness engine for the PSO-based fully-coherent all-sky CBC search
 (Normandin & Mohanty, arXiv:2002.02150): a C-ABI CUDA library (libfcas.so) and its binding."""
 
-from .fcas import (FcasError, Context, fcas_create, fcas_fitness, fcas_destroy, fcas_last_error, fcas_get_info,
+from .fcas import (FcasError, Context, fcas_create, fcas_fitness, fcas_fitness_noalloc, fcas_destroy, fcas_last_error, fcas_get_info,
                    fcas_profile_enable, fcas_profile_read, load_library, LIB_PATH)
 
-__all__ = ["FcasError", "Context", "fcas_create", "fcas_fitness", "fcas_destroy", "fcas_last_error",
+__all__ = ["FcasError", "Context", "fcas_create", "fcas_fitness", "fcas_fitness_noalloc", "fcas_destroy", "fcas_last_error",
            "fcas_get_info", "fcas_profile_enable", "fcas_profile_read", "load_library", "LIB_PATH"]

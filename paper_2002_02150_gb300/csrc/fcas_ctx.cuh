@@ -1,0 +1,77 @@
+// Definition of the opaque fcas_ctx, shared by the translation units that implement the C ABI.
+#pragma once
+
+#include <vector>
+
+#include "fcas_kernels.cuh"
+
+namespace fcas {
+
+// Record `msg` as the calling thread's last error (returned by fcas_last_error) and return `code`.
+int report_error(int code, const char* msg);
+
+struct EventPair {
+    cudaEvent_t a, b;
+    int kind;
+};
+
+}  // namespace fcas
+
+struct fcas_ctx {
+    fcas_setup setup{};
+    int log_n = 0, log_n1 = 0, log_n2 = 0;
+    int64_t n1 = 0, n2 = 0;
+    int64_t k_lo = 0, k_hi = 0;
+    double df = 0.0, scale = 1.0;
+    double sigma2[FCAS_MAX_DET] = {};
+    double* d_det = nullptr;        // [D][9]
+    double* d_sigma2s = nullptr;    // scaled template norms
+    void* d_y = nullptr;            // Y (precision-dependent)
+    void* d_basis = nullptr;
+    void* d_tw = nullptr;           // precision-dependent copies of the twiddle tables
+    void* d_twlo = nullptr;
+    void* d_twhi = nullptr;
+    double2* d_tw64 = nullptr;      // binary64 tables (create path)
+    double2* d_twlo64 = nullptr;
+    double2* d_twhi64 = nullptr;
+    float2* d_tw32 = nullptr;
+    float2* d_twlo32 = nullptr;
+    float2* d_twhi32 = nullptr;
+    fcas::ParticleParams* d_params = nullptr;
+    int64_t params_cap = 0;
+    double* d_theta = nullptr;      // staging for host theta
+    double* d_fit = nullptr;        // staging for host outputs
+    int64_t* d_tc = nullptr;
+    int64_t stage_cap = 0;
+    void* d_inter = nullptr;        // [chunk][D][N2][N1] complex
+    fcas::Partial* d_partials = nullptr;  // [chunk][blocks per particle]
+    int64_t chunk = 0;
+    int64_t nb_partials = 0;
+    // profiling
+    bool prof = false;
+    std::vector<fcas::EventPair> events;
+    size_t events_used = 0;
+};
+
+namespace fcas {
+
+// Pointers and sizes the fitness kernels need, taken from a prepared context.
+inline FitnessPlan make_plan(const fcas_ctx* c) {
+    FitnessPlan p;
+    p.n_det = c->setup.n_det;
+    p.log_n = c->log_n;
+    p.log_n1 = c->log_n1;
+    p.log_n2 = c->log_n2;
+    p.n_samples = c->setup.n_samples;
+    const int log_tw = c->log_n1 > c->log_n2 ? c->log_n1 : c->log_n2;
+    p.tw_shift_a = log_tw - c->log_n2;
+    p.tw_shift_b = log_tw - c->log_n1;
+    p.y = c->d_y;
+    p.basis = c->d_basis;
+    p.tw = c->d_tw;
+    p.tw_lo = c->d_twlo;
+    p.tw_hi = c->d_twhi;
+    return p;
+}
+
+}  // namespace fcas

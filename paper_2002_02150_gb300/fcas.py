@@ -61,6 +61,8 @@ def load_library():
     lib.fcas_create.restype = i32
     lib.fcas_fitness.argtypes = [vp, i64, vp, vp, vp, vp]
     lib.fcas_fitness.restype = i32
+    lib.fcas_fitness_noalloc.argtypes = [vp, i64, vp, vp, vp, vp]
+    lib.fcas_fitness_noalloc.restype = i32
     lib.fcas_destroy.argtypes = [vp]
     lib.fcas_destroy.restype = None
     lib.fcas_last_error.argtypes = []
@@ -179,6 +181,20 @@ def fcas_fitness(ctx, theta, fitness=None, tc=None, stream=None):
     if k3 is not tc and _is_torch(tc):
         tc.copy_(k3)
     return (k2 if not _is_torch(fitness) else fitness), (k3 if not _is_torch(tc) else tc)
+
+
+def fcas_fitness_noalloc(ctx, theta, fitness, tc, stream=None):
+    """Allocation-free evaluation: theta (n, 4), fitness (n,) and tc (n,) must be torch CUDA tensors
+    (float64, float64, int64, contiguous). Scratch comes from the library's fixed static device array."""
+    lib = load_library()
+    for a, dt in ((theta, "torch.float64"), (fitness, "torch.float64"), (tc, "torch.int64")):
+        if not (_is_torch(a) and a.is_cuda and str(a.dtype) == dt and a.is_contiguous()):
+            raise TypeError("fcas_fitness_noalloc needs contiguous CUDA tensors: theta/fitness float64, tc int64")
+    n = int(theta.shape[0])
+    _check(lib.fcas_fitness_noalloc(ctx.handle, n, ctypes.c_void_p(theta.data_ptr()),
+                                    ctypes.c_void_p(fitness.data_ptr()), ctypes.c_void_p(tc.data_ptr()),
+                                    _stream(stream, theta, fitness, tc)))
+    return fitness, tc
 
 
 def fcas_destroy(ctx):
