@@ -218,16 +218,22 @@ def bench_ours(args, ranks):
     chunks_per_step = -(-n // info["chunk"])
     parts = [min(info["chunk"], n - c * info["chunk"]) for c in range(chunks_per_step)]
     mean_p = sum(parts) / len(parts)
-    algo = {"pass_a": mean_p * d * nn * 8 + d * nband * 8, "pass_b": mean_p * d * nn * 8}
+    # pass A writes the two network-weighted series of every particle and reads the band spectrum
+    # once per launch; pass B reads the series back
+    algo = {"pass_a": mean_p * info["inter_bytes"] + d * nband * 8, "pass_b": mean_p * info["inter_bytes"]}
+    peak, peak_kind = measured_peak()
     dom = max(("pass_a", "pass_b"), key=lambda k: kern[k][0])
     ms, launches = kern[dom]
     achieved = algo[dom] / (ms / launches / 1e3) / 1e9
-    peak, peak_kind = measured_peak()
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_source": peak_kind,
                 "traffic": ncu_traffic(dom, w.name), "algorithmic_bytes_per_launch": int(algo[dom]),
                 "launch_ms": round(ms / launches, 4)}
     kernels = {k: {"ms_total": round(v[0], 3), "launches": v[1]} for k, v in kern.items()}
+    for k in ("pass_a", "pass_b"):
+        if kern[k][1]:
+            gbs = algo[k] / (kern[k][0] / kern[k][1] / 1e3) / 1e9
+            kernels[k].update({"algorithmic_gbs": round(gbs, 1), "frac_of_measured_hbm": round(gbs / peak, 4)})
     gpu_launches = sum(v[1] for v in kern.values())
 
     # end to end through the C ABI with host buffers (pinned): H2D of theta, D2H of results
@@ -278,7 +284,7 @@ def bench_ours(args, ranks):
         "config": {"workload": w.name, "detectors": list(w.detectors), "n_fft": w.n_fft, "n_samples": w.n_samples,
                    "fs": w.fs, "band_hz": [w.f_low, w.f_high], "particles_per_gpu": n,
                    "precision": "fp32 + float-float phase", "chunk": info["chunk"],
-                   "l2": "inputs larger than L2 (intermediate %.1f GB per step), no flush" % (n * d * nn * 8 / 1e9)},
+                   "l2": "inputs larger than L2 (intermediate %.1f GB per step), no flush" % (n * info["inter_bytes"] / 1e9)},
         "roofline": roofline, "kernels": kernels, "gpu_launches": gpu_launches, "e2e": e2e, "clocks": clock,
         "fp64_form": fp64,
         "search_time_over_data_time": {"value": round(PSO_EVALS / value / DATA_SECONDS, 5),

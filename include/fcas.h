@@ -116,9 +116,9 @@ int fcas_fitness(fcas_ctx* ctx, int64_t n, const double* theta, double* fitness,
  * Its scratch (per-particle parameters, the intermediate transform between the two FFT passes and
  * the argmax partials) lives in one static device array of 32 MiB inside libfcas.so, which every
  * GPU that loads the library holds until the process exits. One particle needs
- * n_det * n_fft * (8 bytes FP32, 16 bytes FP64) plus ~0.3 KB; particles are processed in chunks
- * that fit. A context whose single particle does not fit (e.g. 4 detectors at n_fft >= 2^20 in
- * FP32) is rejected with FCAS_ERR_INVALID and a message naming the sizes.
+ * 2 * n_fft * (8 bytes FP32, 16 bytes FP64) plus ~0.5 KB; particles are processed in chunks
+ * that fit. A context whose single particle does not fit (n_fft >= 2^21 in FP32, >= 2^20 in FP64)
+ * is rejected with FCAS_ERR_INVALID and a message naming the sizes.
  *
  *   ctx, n, theta, fitness, tc : as for fcas_fitness, except that theta, fitness and tc must be
  *                                device pointers (host arrays would need staging memory):
@@ -152,6 +152,8 @@ typedef struct fcas_info {
     int32_t n_det, precision;
     double scale;               /* power of two applied to the whitened data (Gamma^2 is invariant) */
     double sigma2[FCAS_MAX_DET];/* unscaled template norms <h_c|h_c>^i */
+    int64_t inter_bytes;        /* bytes per particle that cross HBM between the two FFT passes */
+    int64_t series;             /* length-N transforms per particle (2: the network-weighted series) */
 } fcas_info;
 
 int fcas_get_info(const fcas_ctx* ctx, fcas_info* info);

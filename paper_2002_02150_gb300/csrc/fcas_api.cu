@@ -56,8 +56,8 @@ namespace {
 
 void free_ctx(fcas_ctx* c) {
     void* ptrs[] = {c->d_det, c->d_sigma2s, c->d_y, c->d_basis, c->d_tw64, c->d_twlo64, c->d_twhi64,
-                    c->d_tw32, c->d_twlo32, c->d_twhi32, c->d_params, c->d_theta, c->d_fit, c->d_tc,
-                    c->d_inter, c->d_partials};
+                    c->d_tw32, c->d_twlo32, c->d_twhi32, c->d_stw_a64, c->d_stw_a32, c->d_stw_b64, c->d_stw_b32,
+                    c->d_params, c->d_theta, c->d_fit, c->d_tc, c->d_inter, c->d_partials};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& e : c->events) {
@@ -285,6 +285,12 @@ int fcas_create(fcas_ctx** out, const fcas_setup* setup, const fcas_detector* de
     FCAS_TRY(dev_alloc(&c->d_twhi32, sizeof(float2) * nhi, "twiddles"));
     FCAS_TRYCUDA(launch_tables(log_n, c->log_n1, c->log_n2, c->d_tw64, c->d_twlo64, c->d_twhi64, c->d_tw32,
                                c->d_twlo32, c->d_twhi32, st));
+    FCAS_TRY(dev_alloc(&c->d_stw_a64, sizeof(double2) * ((size_t)1 << c->log_n2), "stage twiddles"));
+    FCAS_TRY(dev_alloc(&c->d_stw_a32, sizeof(float2) * ((size_t)1 << c->log_n2), "stage twiddles"));
+    FCAS_TRY(dev_alloc(&c->d_stw_b64, sizeof(double2) * ((size_t)1 << c->log_n1), "stage twiddles"));
+    FCAS_TRY(dev_alloc(&c->d_stw_b32, sizeof(float2) * ((size_t)1 << c->log_n1), "stage twiddles"));
+    FCAS_TRYCUDA(launch_stage_tables(c->log_n2, c->d_stw_a64, c->d_stw_a32, st));
+    FCAS_TRYCUDA(launch_stage_tables(c->log_n1, c->d_stw_b64, c->d_stw_b32, st));
     const bool fp32 = s.precision == FCAS_PREC_FP32;
     c->d_tw = fp32 ? (void*)c->d_tw32 : (void*)c->d_tw64;
     c->d_twlo = fp32 ? (void*)c->d_twlo32 : (void*)c->d_twlo64;
@@ -304,8 +310,7 @@ int fcas_create(fcas_ctx** out, const fcas_setup* setup, const fcas_detector* de
                              c->scale, s.precision, c->d_y, c->d_basis, st));
 
     // scratch for the fitness path
-    const size_t csz = fp32 ? sizeof(float2) : sizeof(double2);
-    const size_t per_particle = csz * (size_t)D * n;
+    const size_t per_particle = inter_bytes_per_particle(s.precision, n);
     int64_t chunk = s.max_batch;
     if (chunk == 0) {
         const size_t budget = (size_t)16 << 30;
@@ -314,7 +319,7 @@ int fcas_create(fcas_ctx** out, const fcas_setup* setup, const fcas_detector* de
         if (chunk < 1) chunk = 1;
     }
     c->chunk = chunk;
-    c->nb_partials = pass_b_blocks_per_particle(c->log_n1, c->log_n2);
+    c->nb_partials = pass_b_blocks_per_particle(c->log_n1, c->log_n2, s.precision);
     FCAS_TRY(dev_alloc(&c->d_inter, per_particle * (size_t)chunk, "intermediate transform"));
     FCAS_TRY(dev_alloc(&c->d_partials, sizeof(Partial) * (size_t)chunk * c->nb_partials, "argmax partials"));
     FCAS_TRYCUDA(cudaStreamSynchronize(st));
@@ -402,6 +407,8 @@ int fcas_get_info(const fcas_ctx* c, fcas_info* info) {
     info->precision = c->setup.precision;
     info->scale = c->scale;
     for (int i = 0; i < c->setup.n_det; ++i) info->sigma2[i] = c->sigma2[i];
+    info->inter_bytes = (int64_t)inter_bytes_per_particle(c->setup.precision, c->setup.n_fft);
+    info->series = kSeries;
     return FCAS_OK;
 }
 

@@ -218,8 +218,9 @@ cudaError_t launch_data_fft(const double* data, int n_det, int64_t n_samples, in
 
 // ------------------------------------------------------------------------------------------
 // Y_i[k] = s 4 df f_k^{-7/6} e^{-i pi/4} dt X~_i[k] / S_i[k] on the band (zero elsewhere), laid out
-// as [i][k1 / K1B][k2 < N2/2][k1 % K1B] with k = k1 + N1 k2, and the float-float chirp basis
-// phi^-5/3, phi^-1, phi^-2/3, phi^-1/3 (phi = f_k / f_*) in the same [k1 / K1B][k2][k1 % K1B] order.
+// as [k1 / K1B][k2 < N2/2][k1 % K1B][i] with k = k1 + N1 k2 (the detectors of one bin adjacent),
+// and the float-float chirp basis phi^-5/3, phi^-1, phi^-2/3, phi^-1/3 (phi = f_k / f_*) in the
+// order [k1 / K1B][k2][k1 % K1B].
 // ------------------------------------------------------------------------------------------
 __global__ void prep_kernel(const double2* __restrict__ spec, const double* __restrict__ psd, int n_det,
                             int64_t psd_row, int log_n, int log_n1, int log_n2, int k1b, int64_t k_lo, int64_t k_hi,
@@ -228,48 +229,46 @@ __global__ void prep_kernel(const double2* __restrict__ spec, const double* __re
     const int64_t n = (int64_t)1 << log_n;
     const int64_t n1 = (int64_t)1 << log_n1;
     const int64_t half2 = ((int64_t)1 << log_n2) / 2;
-    const int64_t per_det = n1 * half2;
-    const int64_t total = per_det * n_det;
+    const int64_t total = n1 * half2;
     const double df = fs / (double)n;
     const double dt = 1.0 / fs;
     const double rs2 = 0.70710678118654752440;
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(g / per_det);
-        const int64_t rem = g % per_det;            // layout index within one detector
-        const int64_t c = rem % k1b;
-        const int64_t k2 = (rem / k1b) % half2;
-        const int64_t blk = rem / (k1b * half2);
+        const int64_t c = g % k1b;
+        const int64_t k2 = (g / k1b) % half2;
+        const int64_t blk = g / (k1b * half2);
         const int64_t k = blk * k1b + c + n1 * k2;
-        double2 yv = make_double2(0.0, 0.0);
+        const bool in_band = k >= k_lo && k <= k_hi;
+        const double f = (double)k * df;
+        for (int i = 0; i < n_det; ++i) {
+            double2 yv = make_double2(0.0, 0.0);
+            if (in_band) {
+                const double2 x = spec[(int64_t)i * n + k];
+                const double a = scale * 4.0 * df * pow(f, -7.0 / 6.0) * dt / psd[i * psd_row + k];
+                // (x.re + i x.im) (1 - i) / sqrt 2
+                yv = make_double2(a * rs2 * (x.x + x.y), a * rs2 * (x.y - x.x));
+            }
+            if (precision == FCAS_PREC_FP32) static_cast<float2*>(y)[g * n_det + i] = make_float2((float)yv.x, (float)yv.y);
+            else static_cast<double2*>(y)[g * n_det + i] = yv;
+        }
         double b53 = 0.0, b1 = 0.0, b23 = 0.0, b13 = 0.0;
-        if (k >= k_lo && k <= k_hi) {
-            const double f = (double)k * df;
-            const double2 x = spec[(int64_t)i * n + k];
-            const double a = scale * 4.0 * df * pow(f, -7.0 / 6.0) * dt / psd[i * psd_row + k];
-            // (x.re + i x.im) (1 - i) / sqrt 2
-            yv = make_double2(a * rs2 * (x.x + x.y), a * rs2 * (x.y - x.x));
+        if (in_band) {
             b1 = f_star / f;
             b13 = cbrt(b1);
             b23 = b13 * b13;
             b53 = b1 * b23;
         }
         if (precision == FCAS_PREC_FP32) {
-            static_cast<float2*>(y)[g] = make_float2((float)yv.x, (float)yv.y);
-            if (i == 0) {
-                BasisF bf;
-                const float h53 = (float)b53, h1 = (float)b1, h23 = (float)b23, h13 = (float)b13;
-                bf.a = make_float4(h53, (float)(b53 - (double)h53), h1, (float)(b1 - (double)h1));
-                bf.b = make_float4(h23, (float)(b23 - (double)h23), h13, (float)(b13 - (double)h13));
-                static_cast<BasisF*>(basis)[rem] = bf;
-            }
+            BasisF bf;
+            const float h53 = (float)b53, h1 = (float)b1, h23 = (float)b23, h13 = (float)b13;
+            bf.a = make_float4(h53, (float)(b53 - (double)h53), h1, (float)(b1 - (double)h1));
+            bf.b = make_float4(h23, (float)(b23 - (double)h23), h13, (float)(b13 - (double)h13));
+            static_cast<BasisF*>(basis)[g] = bf;
         } else {
-            static_cast<double2*>(y)[g] = yv;
-            if (i == 0) {
-                BasisD bd;
-                bd.a = make_double2(b53, b1);
-                bd.b = make_double2(b23, b13);
-                static_cast<BasisD*>(basis)[rem] = bd;
-            }
+            BasisD bd;
+            bd.a = make_double2(b53, b1);
+            bd.b = make_double2(b23, b13);
+            static_cast<BasisD*>(basis)[g] = bd;
         }
     }
 }
@@ -277,7 +276,7 @@ __global__ void prep_kernel(const double2* __restrict__ spec, const double* __re
 cudaError_t launch_prep(const double2* spec, const double* psd, int n_det, int64_t psd_row, int log_n, int log_n1,
                         int log_n2, int64_t k_lo, int64_t k_hi, double fs, double f_star, double scale, int precision,
                         void* y, void* basis, cudaStream_t s) {
-    const int k1b = pass_a_k1b_for(log_n2);
+    const int k1b = pass_a_k1b_for(log_n2, precision);
     if (k1b <= 0) return cudaErrorInvalidValue;
     prep_kernel<<<4096, 256, 0, s>>>(spec, psd, n_det, psd_row, log_n, log_n1, log_n2, k1b, k_lo, k_hi, fs, f_star,
                                      scale, precision, y, basis);

@@ -15,6 +15,11 @@ struct EventPair {
     int kind;
 };
 
+// Bytes of the intermediate transform per particle: two series of N complex values.
+inline size_t inter_bytes_per_particle(int precision, int64_t n_fft) {
+    return (precision == FCAS_PREC_FP32 ? sizeof(float2) : sizeof(double2)) * (size_t)kSeries * (size_t)n_fft;
+}
+
 }  // namespace fcas
 
 struct fcas_ctx {
@@ -37,13 +42,17 @@ struct fcas_ctx {
     float2* d_tw32 = nullptr;
     float2* d_twlo32 = nullptr;
     float2* d_twhi32 = nullptr;
+    double2* d_stw_a64 = nullptr;   // per-stage twiddles, length-N2 transforms
+    float2* d_stw_a32 = nullptr;
+    double2* d_stw_b64 = nullptr;   // per-stage twiddles, length-N1 transforms
+    float2* d_stw_b32 = nullptr;
     fcas::ParticleParams* d_params = nullptr;
     int64_t params_cap = 0;
     double* d_theta = nullptr;      // staging for host theta
     double* d_fit = nullptr;        // staging for host outputs
     int64_t* d_tc = nullptr;
     int64_t stage_cap = 0;
-    void* d_inter = nullptr;        // [chunk][D][N2][N1] complex
+    void* d_inter = nullptr;        // [chunk][2][N2][N1] complex
     fcas::Partial* d_partials = nullptr;  // [chunk][blocks per particle]
     int64_t chunk = 0;
     int64_t nb_partials = 0;
@@ -63,12 +72,11 @@ inline FitnessPlan make_plan(const fcas_ctx* c) {
     p.log_n1 = c->log_n1;
     p.log_n2 = c->log_n2;
     p.n_samples = c->setup.n_samples;
-    const int log_tw = c->log_n1 > c->log_n2 ? c->log_n1 : c->log_n2;
-    p.tw_shift_a = log_tw - c->log_n2;
-    p.tw_shift_b = log_tw - c->log_n1;
+    const bool fp32 = c->setup.precision == FCAS_PREC_FP32;
     p.y = c->d_y;
     p.basis = c->d_basis;
-    p.tw = c->d_tw;
+    p.stw_a = fp32 ? (const void*)c->d_stw_a32 : (const void*)c->d_stw_a64;
+    p.stw_b = fp32 ? (const void*)c->d_stw_b32 : (const void*)c->d_stw_b64;
     p.tw_lo = c->d_twlo;
     p.tw_hi = c->d_twhi;
     return p;

@@ -1,0 +1,219 @@
+// Register-resident Stockham FFT with radix-16 stages, used by both passes of the fitness path.
+//
+// A transform of length L = 2^LOG_L (L >= 16) is held by G = L / 16 threads, thread j owning the
+// 16 values at positions j + q G (q = 0..15) on entry and on exit (natural order). Stage s has
+// radix R_s = 16 while at least four bits of L remain, then one stage takes the remaining 1-3
+// bits; for L < 16 a single stage of radix L is used (V = L values per thread, G = 1). Each stage
+// is the Stockham self-sorting step: task jj reads x[jj + r L/R], multiplies by
+// e^{S 2 pi i r (jj mod Ns) / (Ns R)}, applies the R-point DFT in registers and writes to
+// (jj / Ns) Ns R + (jj mod Ns) + r Ns. Consecutive stages exchange data through shared memory,
+// padded by one element every 16 so that the stride-16 writes of a stage do not share banks.
+// Twiddles come from a per-length table laid out stage by stage as
+//   T[(Ns - 1) + (r - 1) Ns + jm] = e^{2 pi i r jm / (Ns R)},   r = 1..R-1, jm = 0..Ns-1,
+// so that a warp reads consecutive entries; the stages together use L - 1 entries.
+#pragma once
+
+#include "fcas_internal.cuh"
+
+namespace fcas {
+
+__host__ __device__ constexpr int fft16_radix_bits(int log_l, int done) {
+    return (log_l - done) >= 4 ? 4 : (log_l - done);
+}
+__host__ __device__ constexpr int fft16_v(int log_l) { return log_l >= 4 ? 16 : (1 << log_l); }
+__host__ __device__ constexpr int fft16_pad(int e) { return e + (e >> 4); }
+__host__ __device__ constexpr int fft16_buf_elems(int log_l) { return fft16_pad(1 << log_l); }
+
+template <int S, typename C>
+__device__ __forceinline__ void r16_dft4(C& a0, C& a1, C& a2, C& a3) {
+    C t0 = a0 + a2, t1 = a0 - a2, t2 = a1 + a3, t3 = a1 - a3;
+    C it3 = mul_si<S>(t3);
+    a0 = t0 + t2;
+    a2 = t0 - t2;
+    a1 = t1 + it3;
+    a3 = t1 - it3;
+}
+
+// x * e^{S 2 pi i M / 16}
+template <int S, int M, typename C>
+__device__ __forceinline__ C rot16(C x) {
+    using R = decltype(x.x);
+    constexpr int m = M & 15;
+    if constexpr (m == 0) {
+        return x;
+    } else if constexpr (m == 4) {
+        return mul_si<S>(x);
+    } else if constexpr (m == 8) {
+        return mkc(-x.x, -x.y);
+    } else if constexpr (m == 12) {
+        return mul_si<-S>(x);
+    } else {
+        constexpr double kC[16] = {1.0, 0.92387953251128675613, 0.70710678118654752440, 0.38268343236508977173,
+                                   0.0, -0.38268343236508977173, -0.70710678118654752440, -0.92387953251128675613,
+                                   -1.0, -0.92387953251128675613, -0.70710678118654752440, -0.38268343236508977173,
+                                   0.0, 0.38268343236508977173, 0.70710678118654752440, 0.92387953251128675613};
+        constexpr double kS[16] = {0.0, 0.38268343236508977173, 0.70710678118654752440, 0.92387953251128675613,
+                                   1.0, 0.92387953251128675613, 0.70710678118654752440, 0.38268343236508977173,
+                                   0.0, -0.38268343236508977173, -0.70710678118654752440, -0.92387953251128675613,
+                                   -1.0, -0.92387953251128675613, -0.70710678118654752440, -0.38268343236508977173};
+        const R c = (R)kC[m];
+        const R s = (R)(S * kS[m]);
+        if constexpr (m == 2 || m == 6 || m == 10 || m == 14) {
+            // |c| = |s| = 1/sqrt 2: two multiplies instead of four
+            const R k = (R)0.70710678118654752440;
+            const R sc = c > 0 ? (R)1 : (R)-1, ss = s > 0 ? (R)1 : (R)-1;
+            return mkc(k * (sc * x.x - ss * x.y), k * (ss * x.x + sc * x.y));
+        } else {
+            return mkc(x.x * c - x.y * s, x.x * s + x.y * c);
+        }
+    }
+}
+
+template <int S, typename C>
+__device__ __forceinline__ void dft8(C (&a)[8]) {
+    // n = 2 n1 + n2, k = k1 + 4 k2: DFT4 over n1, twiddle e^{S 2 pi i n2 k1 / 8}, DFT2 over n2
+    C e0 = a[0], e1 = a[2], e2 = a[4], e3 = a[6];
+    C o0 = a[1], o1 = a[3], o2 = a[5], o3 = a[7];
+    r16_dft4<S>(e0, e1, e2, e3);
+    r16_dft4<S>(o0, o1, o2, o3);
+    o1 = rot16<S, 2>(o1);
+    o2 = rot16<S, 4>(o2);
+    o3 = rot16<S, 6>(o3);
+    a[0] = e0 + o0;
+    a[4] = e0 - o0;
+    a[1] = e1 + o1;
+    a[5] = e1 - o1;
+    a[2] = e2 + o2;
+    a[6] = e2 - o2;
+    a[3] = e3 + o3;
+    a[7] = e3 - o3;
+}
+
+template <int S, typename C>
+__device__ __forceinline__ void dft16(C (&a)[16]) {
+    // n = 4 n1 + n2, k = k1 + 4 k2: DFT4 over n1 (for each n2), twiddle e^{S 2 pi i n2 k1 / 16},
+    // DFT4 over n2 (for each k1)
+    C y0[4] = {a[0], a[4], a[8], a[12]};
+    C y1[4] = {a[1], a[5], a[9], a[13]};
+    C y2[4] = {a[2], a[6], a[10], a[14]};
+    C y3[4] = {a[3], a[7], a[11], a[15]};
+    r16_dft4<S>(y0[0], y0[1], y0[2], y0[3]);
+    r16_dft4<S>(y1[0], y1[1], y1[2], y1[3]);
+    r16_dft4<S>(y2[0], y2[1], y2[2], y2[3]);
+    r16_dft4<S>(y3[0], y3[1], y3[2], y3[3]);
+    y1[1] = rot16<S, 1>(y1[1]);
+    y1[2] = rot16<S, 2>(y1[2]);
+    y1[3] = rot16<S, 3>(y1[3]);
+    y2[1] = rot16<S, 2>(y2[1]);
+    y2[2] = rot16<S, 4>(y2[2]);
+    y2[3] = rot16<S, 6>(y2[3]);
+    y3[1] = rot16<S, 3>(y3[1]);
+    y3[2] = rot16<S, 6>(y3[2]);
+    y3[3] = rot16<S, 9>(y3[3]);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+        C b0 = y0[k1], b1 = y1[k1], b2 = y2[k1], b3 = y3[k1];
+        r16_dft4<S>(b0, b1, b2, b3);
+        a[k1] = b0;
+        a[k1 + 4] = b1;
+        a[k1 + 8] = b2;
+        a[k1 + 12] = b3;
+    }
+}
+
+template <int S, int R, typename C>
+__device__ __forceinline__ void dft_r(C (&a)[R]) {
+    if constexpr (R == 16) dft16<S>(a);
+    else if constexpr (R == 8) dft8<S>(a);
+    else if constexpr (R == 4) r16_dft4<S>(a[0], a[1], a[2], a[3]);
+    else if constexpr (R == 2) {
+        C t = a[0] - a[1];
+        a[0] = a[0] + a[1];
+        a[1] = t;
+    }
+}
+
+template <typename Real, int S, int LOG_L, int DONE>
+__device__ __forceinline__ void fft16_stage(cplx<Real> (&v)[fft16_v(LOG_L)], cplx<Real>* buf, int es, int j,
+                                            const cplx<Real>* __restrict__ stw) {
+    using C = cplx<Real>;
+    constexpr int L = 1 << LOG_L;
+    constexpr int V = fft16_v(LOG_L);
+    constexpr int G = L / V;
+    constexpr int RB = fft16_radix_bits(LOG_L, DONE);
+    constexpr int R = 1 << RB;
+    constexpr int T = V / R;
+    constexpr int NS = 1 << DONE;
+    constexpr bool FIRST = DONE == 0;
+    constexpr bool LAST = DONE + RB == LOG_L;
+    if constexpr (!FIRST) {
+#pragma unroll
+        for (int q = 0; q < V; ++q) v[q] = buf[fft16_pad(j + q * G) * es];
+    }
+#pragma unroll
+    for (int h = 0; h < T; ++h) {
+        const int jj = j + h * G;
+        C a[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) a[r] = v[h + r * T];
+        if constexpr (NS > 1) {
+            const int jm = jj & (NS - 1);
+            const C* t = stw + (NS - 1) + jm;
+            if constexpr (R >= 8) {
+                // w^r for r = 1..R-1 from two table entries: w and w^4 (powers by products, <= 3 roundings)
+                C w1 = __ldg(t);
+                C w4 = __ldg(t + 3 * NS);
+                if constexpr (S < 0) {
+                    w1 = cconj(w1);
+                    w4 = cconj(w4);
+                }
+                const C w2 = cmul(w1, w1);
+                const C w3 = cmul(w2, w1);
+                a[1] = cmul(a[1], w1);
+                a[2] = cmul(a[2], w2);
+                a[3] = cmul(a[3], w3);
+                C wb = w4;
+#pragma unroll
+                for (int hi = 1; hi < R / 4; ++hi) {
+                    a[4 * hi] = cmul(a[4 * hi], wb);
+                    a[4 * hi + 1] = cmul(a[4 * hi + 1], cmul(wb, w1));
+                    a[4 * hi + 2] = cmul(a[4 * hi + 2], cmul(wb, w2));
+                    a[4 * hi + 3] = cmul(a[4 * hi + 3], cmul(wb, w3));
+                    if (hi + 1 < R / 4) wb = cmul(wb, w4);
+                }
+            } else {
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    C w = __ldg(t + (r - 1) * NS);
+                    if constexpr (S < 0) w = cconj(w);
+                    a[r] = cmul(a[r], w);
+                }
+            }
+        }
+        dft_r<S, R>(a);
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[h + r * T] = a[r];
+    }
+    if constexpr (!LAST) {
+        __syncthreads();
+#pragma unroll
+        for (int h = 0; h < T; ++h) {
+            const int jj = j + h * G;
+            const int dst = (jj / NS) * NS * R + (jj & (NS - 1));
+#pragma unroll
+            for (int r = 0; r < R; ++r) buf[fft16_pad(dst + r * NS) * es] = v[h + r * T];
+        }
+        __syncthreads();
+    }
+}
+
+template <typename Real, int S, int LOG_L, int DONE = 0>
+__device__ __forceinline__ void fft16(cplx<Real> (&v)[fft16_v(LOG_L)], cplx<Real>* buf, int es, int j,
+                                      const cplx<Real>* __restrict__ stw) {
+    if constexpr (DONE < LOG_L) {
+        fft16_stage<Real, S, LOG_L, DONE>(v, buf, es, j, stw);
+        fft16<Real, S, LOG_L, DONE + fft16_radix_bits(LOG_L, DONE)>(v, buf, es, j, stw);
+    }
+}
+
+}  // namespace fcas

@@ -54,25 +54,41 @@ struct ParticleParams {
     double u[FCAS_MAX_DET][2];     // U^i = (F+, Fx)(alpha, delta, psi = 0)
     double ginv[3];                // (G^-1)_{11}, (G^-1)_{12}, (G^-1)_{22} with the scaled template norms
     double chol[3];                // G^-1 = L L^T, L = [[l11, 0], [l21, l22]]: (l11, l21, l22)
+    // Network weights: Gamma^2(t) = |sum_i w1_i Z_i(t)|^2 + |sum_i w2_i Z_i(t)|^2 with
+    // w1_i = l11 U+^i + l21 Ux^i, w2_i = l22 Ux^i (L^T applied to U).
+    double w1[FCAS_MAX_DET], w2[FCAS_MAX_DET];
+    // float-float copies for the FP32 form (hi + lo)
+    float ch[4], cl[4];
+    float dh[FCAS_MAX_DET], dl[FCAS_MAX_DET];
+    float w1f[FCAS_MAX_DET], w2f[FCAS_MAX_DET];
     int32_t valid;                 // 0: non-finite / non-positive input -> fitness NaN, tc -1
     int32_t pad;
 };
 
 // ------------------------------------------------------------------------------------------
 // Launch shapes. Pass A transforms columns of length N2 (K1B columns per CTA), pass B rows of
-// length N1 (TB rows per CTA). Every thread owns V values of a transform.
+// length N1 (TB rows per CTA); each transform is held by L / V threads with V = min(16, L)
+// values per thread. Pass A also keeps K1B <= L so that K1B divides N1 (N1 >= N2 = L).
 // ------------------------------------------------------------------------------------------
-__host__ __device__ constexpr int pass_a_v(int log_l) { return log_l >= 10 ? 16 : (log_l >= 3 ? 8 : 4); }
-__host__ __device__ constexpr int pass_a_threads_target(int log_l) { return log_l >= 10 ? 512 : 256; }
 __host__ __device__ constexpr int imin_c(int a, int b) { return a < b ? a : b; }
 __host__ __device__ constexpr int imax_c(int a, int b) { return a > b ? a : b; }
-__host__ __device__ constexpr int pass_a_k1b(int log_l) {
-    return imin_c(imin_c(16, imax_c(1, pass_a_threads_target(log_l) / ((1 << log_l) / pass_a_v(log_l)))), 1 << log_l);
+__host__ __device__ constexpr int shape_v(int log_l) { return log_l >= 4 ? 16 : (1 << log_l); }
+__host__ __device__ constexpr int pass_a_k1b(int log_l, int real_bytes) {
+    return imin_c(imin_c(16, imax_c(1, (real_bytes == 4 ? 512 : 256) / ((1 << log_l) / shape_v(log_l)))),
+                  1 << log_l);
 }
-__host__ __device__ constexpr int pass_b_v(int log_l) { return log_l >= 3 ? 8 : 4; }
-__host__ __device__ constexpr int pass_b_tb(int log_l) {
-    return imin_c(imin_c(16, imax_c(1, 256 / ((1 << log_l) / pass_b_v(log_l)))), (1 << log_l) / 2);
+__host__ __device__ constexpr int pass_a_threads(int log_l, int real_bytes) {
+    return pass_a_k1b(log_l, real_bytes) * ((1 << log_l) / shape_v(log_l));
 }
+__host__ __device__ constexpr int pass_b_tb(int log_l, int real_bytes) {
+    return imin_c(imin_c(16, imax_c(1, (real_bytes == 4 ? 256 : 128) / ((1 << log_l) / shape_v(log_l)))),
+                  (1 << log_l) / 2);
+}
+__host__ __device__ constexpr int pass_b_threads(int log_l, int real_bytes) {
+    return pass_b_tb(log_l, real_bytes) * ((1 << log_l) / shape_v(log_l));
+}
+// Transforms per particle between the passes: the two network-weighted series.
+constexpr int kSeries = 2;
 
 // Smallest/largest supported transform lengths.
 constexpr int kMinLogN = 4;

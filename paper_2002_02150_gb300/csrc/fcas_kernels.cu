@@ -4,10 +4,13 @@
 // k = k1 + N1 k2 and t = ta + N2 tb:
 //   Z[ta + N2 tb] = sum_k1 e^{2 pi i k1 tb / N1} [ e^{2 pi i k1 ta / N} sum_k2 Q[k1 + N1 k2] e^{2 pi i k2 ta / N2} ]
 // Pass A computes the bracket for every column k1 (length-N2 transforms) and stores it as
-// A[ta][k1]; pass B transforms every row ta over k1 (length N1).
+// A[ta][k1]; pass B transforms every row ta over k1 (length N1). Only two series per particle
+// cross between the passes: the detector sum is taken with the network weights before the
+// transform (see pass A).
 #include <cfloat>
+#include <climits>
 
-#include "fcas_fft.cuh"
+#include "fcas_fft16.cuh"
 #include "fcas_kernels.cuh"
 
 namespace fcas {
@@ -25,7 +28,7 @@ __global__ void geometry_kernel(const double* __restrict__ theta, int64_t n, Par
     const double tau0 = theta[4 * p + 2], tau15 = theta[4 * p + 3];
     ParticleParams pp;
     for (int q = 0; q < 4; ++q) pp.c[q] = 0.0;
-    for (int i = 0; i < FCAS_MAX_DET; ++i) pp.dturn[i] = pp.u[i][0] = pp.u[i][1] = 0.0;
+    for (int i = 0; i < FCAS_MAX_DET; ++i) pp.dturn[i] = pp.u[i][0] = pp.u[i][1] = pp.w1[i] = pp.w2[i] = 0.0;
     pp.ginv[0] = pp.ginv[1] = pp.ginv[2] = 0.0;
     pp.chol[0] = pp.chol[1] = pp.chol[2] = 0.0;
     pp.valid = 0;
@@ -84,6 +87,10 @@ __global__ void geometry_kernel(const double* __restrict__ theta, int64_t n, Par
         } else {
             pp.chol[2] = sqrt(fmax(0.0, pp.ginv[2]));
         }
+        for (int i = 0; i < n_det; ++i) {
+            pp.w1[i] = pp.chol[0] * pp.u[i][0] + pp.chol[1] * pp.u[i][1];
+            pp.w2[i] = pp.chol[2] * pp.u[i][1];
+        }
         // (tau0, tau1.5) -> x = pi M f_*, eta; then the 2PN chirp times tau1, tau2.
         const double pi = 0.5 * kTwoPi;
         const double x = 5.0 * tau15 / (32.0 * pi * tau0);
@@ -97,6 +104,17 @@ __global__ void geometry_kernel(const double* __restrict__ theta, int64_t n, Par
         pp.c[2] = -1.5 * f_star * tau15;
         pp.c[3] = 3.0 * f_star * tau2;
         pp.valid = 1;
+    }
+    for (int r = 0; r < 4; ++r) {
+        pp.ch[r] = (float)pp.c[r];
+        pp.cl[r] = (float)(pp.c[r] - (double)pp.ch[r]);
+    }
+    for (int i = 0; i < FCAS_MAX_DET; ++i) {
+        if (i >= n_det) pp.w1[i] = pp.w2[i] = 0.0;
+        pp.dh[i] = (float)pp.dturn[i];
+        pp.dl[i] = (float)(pp.dturn[i] - (double)pp.dh[i]);
+        pp.w1f[i] = (float)pp.w1[i];
+        pp.w2f[i] = (float)pp.w2[i];
     }
     out[p] = pp;
 }
@@ -162,144 +180,177 @@ __device__ __forceinline__ double2 unit_phasor(double turns) {
 }
 
 // ------------------------------------------------------------------------------------------
-// Pass A
+// Pass A: for every band bin of the CTA's columns, Q_i[k] = Y_i[k] e^{2 pi i (psi(f_k)/2pi + f_k Delta^i)}
+// is generated on the load and combined over detectors into the two network-weighted spectra
+// P_a[k] = sum_i w_a,i Q_i[k] (a = 1, 2); each is transformed over k2 (length N2) and twiddled by
+// e^{2 pi i k1 ta / N}. By linearity of the transform over t_c, Z-projections
+// W_a(t) = sum_i w_a,i Z_i(t) are the transforms of P_a (Sec. II.C projection applied before the
+// t_c scan instead of after it).
 // ------------------------------------------------------------------------------------------
+template <typename Real>
+struct DetConst {
+    Real dh[FCAS_MAX_DET], dl[FCAS_MAX_DET], w1[FCAS_MAX_DET], w2[FCAS_MAX_DET];
+};
+
 template <typename Real, int LOG_L>
-__global__ void __launch_bounds__(pass_a_k1b(LOG_L) * ((1 << LOG_L) / pass_a_v(LOG_L)))
+__global__ void __launch_bounds__(pass_a_threads(LOG_L, sizeof(Real)), 1)
 pass_a_kernel(const cplx<Real>* __restrict__ y, const Basis<Real>* __restrict__ basis,
               const ParticleParams* __restrict__ params, int64_t p0, int n_det, int log_n1,
-              cplx<Real>* __restrict__ out, const cplx<Real>* __restrict__ tw, int tw_shift,
+              cplx<Real>* __restrict__ out, const cplx<Real>* __restrict__ stw,
               const cplx<Real>* __restrict__ tw_lo, const cplx<Real>* __restrict__ tw_hi) {
     using C = cplx<Real>;
     constexpr int L = 1 << LOG_L;
-    constexpr int V = pass_a_v(LOG_L);
+    constexpr int V = shape_v(LOG_L);
     constexpr int G = L / V;
-    constexpr int K1B = pass_a_k1b(LOG_L);
+    constexpr int K1B = pass_a_k1b(LOG_L, sizeof(Real));
     constexpr int VH = V / 2;    // values with k2 < L/2; the rest of the column is zero (k >= N/2)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* smem = reinterpret_cast<C*>(smem_raw);
+    __shared__ DetConst<Real> sc;
 
     const int c = threadIdx.x % K1B;
     const int j = threadIdx.x / K1B;
     const int blk = blockIdx.y;
     const int k1 = blk * K1B + c;
     const int64_t p = blockIdx.x;
-    const ParticleParams& pp = params[p0 + p];
-    const int64_t n1 = (int64_t)1 << log_n1;
-    const int64_t nblk = n1 / K1B;
-
-    Real chirp[VH];
-    Real kf[VH];
-    ChirpF cf;
-    if constexpr (sizeof(Real) == 4) {
-#pragma unroll
-        for (int r = 0; r < 4; ++r) split_ff(pp.c[r], cf.ch[r], cf.cl[r]);
+    const ParticleParams* pp = params + p0 + p;
+    if (threadIdx.x < FCAS_MAX_DET) {
+        const int i = threadIdx.x;
+        if constexpr (sizeof(Real) == 4) {
+            sc.dh[i] = pp->dh[i];
+            sc.dl[i] = pp->dl[i];
+            sc.w1[i] = pp->w1f[i];
+            sc.w2[i] = pp->w2f[i];
+        } else {
+            sc.dh[i] = pp->dturn[i];
+            sc.dl[i] = 0.0;
+            sc.w1[i] = pp->w1[i];
+            sc.w2[i] = pp->w2[i];
+        }
     }
-    const Basis<Real>* bcol = basis + (int64_t)blk * (L / 2) * K1B + c;
-#pragma unroll
-    for (int q = 0; q < VH; ++q) {
-        const int k2 = j + q * G;
-        kf[q] = (Real)(k1 + n1 * k2);
-        const Basis<Real> b = bcol[(int64_t)k2 * K1B];
-        if constexpr (sizeof(Real) == 4) chirp[q] = chirp_frac(b, cf);
-        else chirp[q] = chirp_frac(b, pp);
-    }
+    __syncthreads();
+    const int n1 = 1 << log_n1;
 
-    for (int i = 0; i < n_det; ++i) {
-        float dh = 0.f, dl = 0.f;
-        if constexpr (sizeof(Real) == 4) split_ff(pp.dturn[i], dh, dl);
-        const C* ycol = y + ((int64_t)i * nblk + blk) * (L / 2) * K1B + c;
-        C v[V];
+    C r1[VH], r2[VH];
+    {
+        float cfh[4], cfl[4];
+        if constexpr (sizeof(Real) == 4) {
 #pragma unroll
-        for (int q = 0; q < VH; ++q) {
-            const C yv = ycol[(int64_t)(j + q * G) * K1B];
-            Real th;
-            if constexpr (sizeof(Real) == 4) {
-                th = chirp[q] + frac_mul_ff(kf[q], 0.0f, dh, dl);
-            } else {
-                th = chirp[q] + kf[q] * pp.dturn[i];
+            for (int r = 0; r < 4; ++r) {
+                cfh[r] = pp->ch[r];
+                cfl[r] = pp->cl[r];
             }
-            th -= round_nearest(th);
-            v[q] = cmul(yv, unit_phasor(th));
         }
 #pragma unroll
+        for (int q = 0; q < VH; ++q) {
+            const int k2 = j + q * G;
+            const int kk = k1 + n1 * k2;
+            const int64_t bin = ((int64_t)blk * (L / 2) + k2) * K1B + c;
+            const Basis<Real> b = basis[bin];
+            Real ph;
+            if constexpr (sizeof(Real) == 4) {
+                float s = frac_mul_ff(cfh[0], cfl[0], b.a.x, b.a.y);
+                s += frac_mul_ff(cfh[1], cfl[1], b.a.z, b.a.w);
+                s += frac_mul_ff(cfh[2], cfl[2], b.b.x, b.b.y);
+                s += frac_mul_ff(cfh[3], cfl[3], b.b.z, b.b.w);
+                ph = s - rintf(s);
+            } else {
+                ph = chirp_frac(b, *pp);
+            }
+            const C* yb = y + bin * n_det;
+            C a1 = mkc((Real)0, (Real)0), a2 = mkc((Real)0, (Real)0);
+            const Real kf = (Real)kk;
+            for (int i = 0; i < n_det; ++i) {
+                const C yv = yb[i];
+                Real th;
+                if constexpr (sizeof(Real) == 4) th = ph + frac_mul_ff(kf, 0.0f, sc.dh[i], sc.dl[i]);
+                else th = ph + kf * sc.dh[i];
+                th -= round_nearest(th);
+                const C qv = cmul(yv, unit_phasor(th));
+                a1.x += sc.w1[i] * qv.x;
+                a1.y += sc.w1[i] * qv.y;
+                a2.x += sc.w2[i] * qv.x;
+                a2.y += sc.w2[i] * qv.y;
+            }
+            r1[q] = a1;
+            r2[q] = a2;
+        }
+    }
+
+#pragma unroll 1
+    for (int a = 0; a < kSeries; ++a) {
+        C v[V];
+#pragma unroll
+        for (int q = 0; q < VH; ++q) v[q] = a == 0 ? r1[q] : r2[q];
+#pragma unroll
         for (int q = VH; q < V; ++q) v[q] = mkc((Real)0, (Real)0);
-
-        block_fft<Real, +1, LOG_L, V>(v, smem + c, K1B, j, tw, tw_shift);
-
-        C* orow = out + (((int64_t)p * n_det + i) * L) * n1 + k1;
+        fft16<Real, +1, LOG_L>(v, smem + c, K1B, j, stw);
+        C* orow = out + ((p * kSeries + a) * L) * (int64_t)n1 + k1;
+        // e^{2 pi i k1 ta / N} for ta = j + q G: the value at q = 0 times powers of the step e^{2 pi i k1 G / N}
+        const int m0 = k1 * j, ms = k1 * G;   // < N
+        C w = cmul(__ldg(tw_hi + (m0 >> kTwLoBits)), __ldg(tw_lo + (m0 & ((1 << kTwLoBits) - 1))));
+        const C step = cmul(__ldg(tw_hi + (ms >> kTwLoBits)), __ldg(tw_lo + (ms & ((1 << kTwLoBits) - 1))));
 #pragma unroll
         for (int q = 0; q < V; ++q) {
             const int ta = j + q * G;
-            const int m = k1 * ta;   // < N
-            const C w = cmul(__ldg(tw_hi + (m >> kTwLoBits)), __ldg(tw_lo + (m & ((1 << kTwLoBits) - 1))));
             orow[(int64_t)ta * n1] = cmul(v[q], w);
+            if (q + 1 < V) w = cmul(w, step);
         }
     }
 }
 
 // ------------------------------------------------------------------------------------------
-// Pass B + antenna projection + partial argmax (Sec. II.C: analytic maximisation over A_k)
+// Pass B: transforms every row ta of both series over k1 (length N1), Gamma^2(t) = |W1(t)|^2 +
+// |W2(t)|^2 for t = ta + N2 tb (Sec. II.C, the maximisation over A_k in closed form), and the
+// argmax over the CTA's rows (lowest t on ties).
 // ------------------------------------------------------------------------------------------
-__device__ __forceinline__ bool better(double v, int64_t t, double bv, int64_t bt) {
+__device__ __forceinline__ bool better_f(float v, int t, float bv, int bt) {
     return v > bv || (v == bv && t < bt);
 }
 
 template <typename Real, int LOG_L>
-__global__ void __launch_bounds__(pass_b_tb(LOG_L) * ((1 << LOG_L) / pass_b_v(LOG_L)))
-pass_b_kernel(const cplx<Real>* __restrict__ inter, const ParticleParams* __restrict__ params, int64_t p0,
-              int n_det, int log_n2, int64_t n_samples, const cplx<Real>* __restrict__ tw, int tw_shift,
-              Partial* __restrict__ partials) {
+__global__ void __launch_bounds__(pass_b_threads(LOG_L, sizeof(Real)), 2)
+pass_b_kernel(const cplx<Real>* __restrict__ inter, int log_n2, int64_t n_samples,
+              const cplx<Real>* __restrict__ stw, Partial* __restrict__ partials) {
     using C = cplx<Real>;
     constexpr int L = 1 << LOG_L;
-    constexpr int V = pass_b_v(LOG_L);
+    constexpr int V = shape_v(LOG_L);
     constexpr int G = L / V;
-    constexpr int TB = pass_b_tb(LOG_L);
+    constexpr int TB = pass_b_tb(LOG_L, sizeof(Real));
     constexpr int NT = TB * G;
+    constexpr int BUF = fft16_buf_elems(LOG_L);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* smem = reinterpret_cast<C*>(smem_raw);
     constexpr int NRED = NT >= 32 ? NT / 32 : NT;
-    __shared__ double red_v[NRED];
-    __shared__ int64_t red_t[NRED];
+    __shared__ Real red_v[NRED];
+    __shared__ int red_t[NRED];
 
     const int j = threadIdx.x % G;
     const int c = threadIdx.x / G;
-    const int64_t n2 = (int64_t)1 << log_n2;
-    const int64_t ta = (int64_t)blockIdx.x * TB + c;
+    const int n2 = 1 << log_n2;
+    const int ta = blockIdx.x * TB + c;
     const int64_t p = blockIdx.y;
-    const ParticleParams& pp = params[p0 + p];
 
-    C w1[V], w2[V];
+    Real g[V];
 #pragma unroll
-    for (int q = 0; q < V; ++q) w1[q] = w2[q] = mkc((Real)0, (Real)0);
-
-    for (int i = 0; i < n_det; ++i) {
-        const C* row = inter + (((int64_t)p * n_det + i) * n2 + ta) * L;
+    for (int q = 0; q < V; ++q) g[q] = (Real)0;
+#pragma unroll 1
+    for (int a = 0; a < kSeries; ++a) {
+        const C* row = inter + ((p * kSeries + a) * n2 + ta) * (int64_t)L;
         C v[V];
 #pragma unroll
         for (int q = 0; q < V; ++q) v[q] = row[j + q * G];
-        block_fft<Real, +1, LOG_L, V>(v, smem + c * L, 1, j, tw, tw_shift);
-        const Real up = (Real)pp.u[i][0], ux = (Real)pp.u[i][1];
+        fft16<Real, +1, LOG_L>(v, smem + c * BUF, 1, j, stw);
 #pragma unroll
-        for (int q = 0; q < V; ++q) {
-            w1[q].x += up * v[q].x;
-            w1[q].y += up * v[q].y;
-            w2[q].x += ux * v[q].x;
-            w2[q].y += ux * v[q].y;
-        }
+        for (int q = 0; q < V; ++q) g[q] += v[q].x * v[q].x + v[q].y * v[q].y;
     }
-    const Real l11 = (Real)pp.chol[0], l21 = (Real)pp.chol[1], l22 = (Real)pp.chol[2];
-    double best = -DBL_MAX;
-    int64_t bt = INT64_MAX;
+    Real best = (Real)-1;
+    int bt = INT_MAX;
 #pragma unroll
     for (int q = 0; q < V; ++q) {
-        const int64_t t = ta + n2 * (j + q * G);
-        // Gamma^2(t) = W^H G^-1 W = |l11 W+ + l21 Wx|^2 + |l22 Wx|^2, W_a = sum_i U_a^i Z_i(t)
-        const Real ax = l11 * w1[q].x + l21 * w2[q].x, ay = l11 * w1[q].y + l21 * w2[q].y;
-        const Real bx = l22 * w2[q].x, by = l22 * w2[q].y;
-        const double gam = (double)(ax * ax + ay * ay + bx * bx + by * by);
-        if (t < n_samples && better(gam, t, best, bt)) {
-            best = gam;
+        const int t = ta + n2 * (j + q * G);
+        if (t < n_samples && (g[q] > best || (g[q] == best && t < bt))) {
+            best = g[q];
             bt = t;
         }
     }
@@ -307,17 +358,16 @@ pass_b_kernel(const cplx<Real>* __restrict__ inter, const ParticleParams* __rest
         // NT is a multiple of 32: every warp is full
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
-            const double ov = __shfl_down_sync(0xffffffffu, best, off);
-            const int64_t ot = __shfl_down_sync(0xffffffffu, bt, off);
-            if (better(ov, ot, best, bt)) { best = ov; bt = ot; }
+            const Real ov = __shfl_down_sync(0xffffffffu, best, off);
+            const int ot = __shfl_down_sync(0xffffffffu, bt, off);
+            if (ov > best || (ov == best && ot < bt)) { best = ov; bt = ot; }
         }
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
         if (lane == 0) { red_v[warp] = best; red_t[warp] = bt; }
         __syncthreads();
         if (threadIdx.x == 0) {
             for (int w = 1; w < NT / 32; ++w)
-                if (better(red_v[w], red_t[w], best, bt)) { best = red_v[w]; bt = red_t[w]; }
-            partials[p * gridDim.x + blockIdx.x] = Partial{best, bt};
+                if (red_v[w] > best || (red_v[w] == best && red_t[w] < bt)) { best = red_v[w]; bt = red_t[w]; }
         }
     } else {
         // fewer than 32 threads: no shuffles over lanes that do not exist
@@ -326,11 +376,18 @@ pass_b_kernel(const cplx<Real>* __restrict__ inter, const ParticleParams* __rest
         __syncthreads();
         if (threadIdx.x == 0) {
             for (int w = 1; w < NT; ++w)
-                if (better(red_v[w], red_t[w], best, bt)) { best = red_v[w]; bt = red_t[w]; }
-            partials[p * gridDim.x + blockIdx.x] = Partial{best, bt};
+                if (red_v[w] > best || (red_v[w] == best && red_t[w] < bt)) { best = red_v[w]; bt = red_t[w]; }
         }
     }
+    if (threadIdx.x == 0)
+        partials[p * gridDim.x + blockIdx.x] = Partial{bt == INT_MAX ? -DBL_MAX : (double)best,
+                                                       bt == INT_MAX ? INT64_MAX : (int64_t)bt};
 }
+
+__device__ __forceinline__ bool better(double v, int64_t t, double bv, int64_t bt) {
+    return v > bv || (v == bv && t < bt);
+}
+
 
 __global__ void reduce_kernel(const Partial* __restrict__ partials, int64_t nb, const ParticleParams* __restrict__ params,
                               int64_t p0, double* __restrict__ fitness, int64_t* __restrict__ tc) {
@@ -371,21 +428,23 @@ cudaError_t launch_reduce(const Partial* partials, int64_t nb, const ParticlePar
 // ------------------------------------------------------------------------------------------
 // dispatch on the transform lengths
 // ------------------------------------------------------------------------------------------
-int pass_a_k1b_for(int log_n2) {
+#define FCAS_LOG_CASES(X) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12)
+
+int pass_a_k1b_for(int log_n2, int precision) {
+    const int rb = precision == FCAS_PREC_FP32 ? 4 : 8;
     switch (log_n2) {
-#define FCAS_CASE(LG) case LG: return pass_a_k1b(LG);
-        FCAS_CASE(2) FCAS_CASE(3) FCAS_CASE(4) FCAS_CASE(5) FCAS_CASE(6) FCAS_CASE(7) FCAS_CASE(8)
-        FCAS_CASE(9) FCAS_CASE(10) FCAS_CASE(11) FCAS_CASE(12)
+#define FCAS_CASE(LG) case LG: return pass_a_k1b(LG, rb);
+        FCAS_LOG_CASES(FCAS_CASE)
 #undef FCAS_CASE
         default: return -1;
     }
 }
 
-int pass_b_blocks_per_particle(int log_n1, int log_n2) {
+int pass_b_blocks_per_particle(int log_n1, int log_n2, int precision) {
+    const int rb = precision == FCAS_PREC_FP32 ? 4 : 8;
     switch (log_n1) {
-#define FCAS_CASE(LG) case LG: return (1 << log_n2) / pass_b_tb(LG);
-        FCAS_CASE(2) FCAS_CASE(3) FCAS_CASE(4) FCAS_CASE(5) FCAS_CASE(6) FCAS_CASE(7) FCAS_CASE(8)
-        FCAS_CASE(9) FCAS_CASE(10) FCAS_CASE(11) FCAS_CASE(12)
+#define FCAS_CASE(LG) case LG: return (1 << log_n2) / pass_b_tb(LG, rb);
+        FCAS_LOG_CASES(FCAS_CASE)
 #undef FCAS_CASE
         default: return -1;
     }
@@ -394,32 +453,32 @@ int pass_b_blocks_per_particle(int log_n1, int log_n2) {
 template <typename Real, int LG>
 static cudaError_t pass_a_at(const FitnessPlan& pl, const ParticleParams* params, int64_t p0, int64_t np, void* inter,
                              cudaStream_t s) {
-    constexpr int K1B = pass_a_k1b(LG);
-    constexpr int THREADS = K1B * ((1 << LG) / pass_a_v(LG));
-    const size_t smem = sizeof(cplx<Real>) * (size_t)K1B * (1 << LG);
+    constexpr int K1B = pass_a_k1b(LG, sizeof(Real));
+    constexpr int THREADS = pass_a_threads(LG, sizeof(Real));
+    const size_t smem = sizeof(cplx<Real>) * (size_t)K1B * fft16_buf_elems(LG);
     auto kern = pass_a_kernel<Real, LG>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)np, (unsigned)((1 << pl.log_n1) / K1B));
     kern<<<grid, THREADS, smem, s>>>(static_cast<const cplx<Real>*>(pl.y), static_cast<const Basis<Real>*>(pl.basis),
                                      params, p0, pl.n_det, pl.log_n1, static_cast<cplx<Real>*>(inter),
-                                     static_cast<const cplx<Real>*>(pl.tw), pl.tw_shift_a,
-                                     static_cast<const cplx<Real>*>(pl.tw_lo), static_cast<const cplx<Real>*>(pl.tw_hi));
+                                     static_cast<const cplx<Real>*>(pl.stw_a), static_cast<const cplx<Real>*>(pl.tw_lo),
+                                     static_cast<const cplx<Real>*>(pl.tw_hi));
     return cudaGetLastError();
 }
 
 template <typename Real, int LG>
-static cudaError_t pass_b_at(const FitnessPlan& pl, const ParticleParams* params, int64_t p0, int64_t np,
-                             const void* inter, Partial* partials, cudaStream_t s) {
-    constexpr int TB = pass_b_tb(LG);
-    constexpr int THREADS = TB * ((1 << LG) / pass_b_v(LG));
-    const size_t smem = sizeof(cplx<Real>) * (size_t)TB * (1 << LG);
+static cudaError_t pass_b_at(const FitnessPlan& pl, int64_t np, const void* inter, Partial* partials,
+                             cudaStream_t s) {
+    constexpr int TB = pass_b_tb(LG, sizeof(Real));
+    constexpr int THREADS = pass_b_threads(LG, sizeof(Real));
+    const size_t smem = sizeof(cplx<Real>) * (size_t)TB * fft16_buf_elems(LG);
     auto kern = pass_b_kernel<Real, LG>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((1 << pl.log_n2) / TB), (unsigned)np);
-    kern<<<grid, THREADS, smem, s>>>(static_cast<const cplx<Real>*>(inter), params, p0, pl.n_det, pl.log_n2,
-                                     pl.n_samples, static_cast<const cplx<Real>*>(pl.tw), pl.tw_shift_b, partials);
+    kern<<<grid, THREADS, smem, s>>>(static_cast<const cplx<Real>*>(inter), pl.log_n2, pl.n_samples,
+                                     static_cast<const cplx<Real>*>(pl.stw_b), partials);
     return cudaGetLastError();
 }
 
@@ -429,8 +488,7 @@ cudaError_t launch_pass_a(const FitnessPlan& pl, const ParticleParams* params, i
     if (np <= 0) return cudaSuccess;
     switch (pl.log_n2) {
 #define FCAS_CASE(LG) case LG: return pass_a_at<Real, LG>(pl, params, p0, np, inter, s);
-        FCAS_CASE(2) FCAS_CASE(3) FCAS_CASE(4) FCAS_CASE(5) FCAS_CASE(6) FCAS_CASE(7) FCAS_CASE(8)
-        FCAS_CASE(9) FCAS_CASE(10) FCAS_CASE(11) FCAS_CASE(12)
+        FCAS_LOG_CASES(FCAS_CASE)
 #undef FCAS_CASE
         default: return cudaErrorInvalidValue;
     }
@@ -439,11 +497,12 @@ cudaError_t launch_pass_a(const FitnessPlan& pl, const ParticleParams* params, i
 template <typename Real>
 cudaError_t launch_pass_b(const FitnessPlan& pl, const ParticleParams* params, int64_t p0, int64_t np,
                           const void* inter, Partial* partials, cudaStream_t s) {
+    (void)params;
+    (void)p0;
     if (np <= 0) return cudaSuccess;
     switch (pl.log_n1) {
-#define FCAS_CASE(LG) case LG: return pass_b_at<Real, LG>(pl, params, p0, np, inter, partials, s);
-        FCAS_CASE(2) FCAS_CASE(3) FCAS_CASE(4) FCAS_CASE(5) FCAS_CASE(6) FCAS_CASE(7) FCAS_CASE(8)
-        FCAS_CASE(9) FCAS_CASE(10) FCAS_CASE(11) FCAS_CASE(12)
+#define FCAS_CASE(LG) case LG: return pass_b_at<Real, LG>(pl, np, inter, partials, s);
+        FCAS_LOG_CASES(FCAS_CASE)
 #undef FCAS_CASE
         default: return cudaErrorInvalidValue;
     }
@@ -455,5 +514,38 @@ template cudaError_t launch_pass_b<float>(const FitnessPlan&, const ParticlePara
                                           Partial*, cudaStream_t);
 template cudaError_t launch_pass_b<double>(const FitnessPlan&, const ParticleParams*, int64_t, int64_t, const void*,
                                            Partial*, cudaStream_t);
+
+// ------------------------------------------------------------------------------------------
+// per-stage twiddle tables of the radix-16 transforms (create time)
+// ------------------------------------------------------------------------------------------
+__global__ void stage_table_kernel(int log_l, double2* t64, float2* t32) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    const int l = 1 << log_l;
+    if (m >= l) return;
+    double2 val = make_double2(1.0, 0.0);
+    // find the stage that owns entry m: (Ns - 1) <= m < Ns R - 1
+    for (int done = 0; done < log_l; done += fft16_radix_bits(log_l, done)) {
+        const int ns = 1 << done;
+        const int r_ = 1 << fft16_radix_bits(log_l, done);
+        if (ns > 1 && m >= ns - 1 && m < ns * r_ - 1) {
+            const int off = m - (ns - 1);
+            const int r = off / ns + 1;
+            const int jm = off % ns;
+            double sn, cs;
+            // e^{2 pi i r jm / (Ns R)}, argument reduced exactly before sincospi
+            const long long num = ((long long)r * jm) % ((long long)ns * r_);
+            sincospi(2.0 * (double)num / (double)(ns * r_), &sn, &cs);
+            val = make_double2(cs, sn);
+        }
+    }
+    t64[m] = val;
+    t32[m] = make_float2((float)val.x, (float)val.y);
+}
+
+cudaError_t launch_stage_tables(int log_l, double2* t64, float2* t32, cudaStream_t s) {
+    const int l = 1 << log_l;
+    stage_table_kernel<<<(l + 255) / 256, 256, 0, s>>>(log_l, t64, t32);
+    return cudaGetLastError();
+}
 
 }  // namespace fcas

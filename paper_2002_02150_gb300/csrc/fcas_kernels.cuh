@@ -29,10 +29,10 @@ struct FitnessPlan {
     int n_det;
     int log_n, log_n1, log_n2;
     int64_t n_samples;
-    int tw_shift_a, tw_shift_b;   // log2(table length / transform length)
-    const void* y;                // Y layout [i][k1 / K1B][k2 < N2/2][k1 % K1B]
+    const void* y;                // Y layout [k1 / K1B][k2 < N2/2][k1 % K1B][i]
     const void* basis;            // basis layout [k1 / K1B][k2 < N2/2][k1 % K1B]
-    const void* tw;               // e^{2 pi i m / TWL}, TWL = max(N1, N2)
+    const void* stw_a;            // per-stage twiddles of the length-N2 transforms
+    const void* stw_b;            // per-stage twiddles of the length-N1 transforms
     const void* tw_lo;            // e^{2 pi i m / N}, m < 4096
     const void* tw_hi;            // e^{2 pi i 4096 m / N}, m < max(1, N / 4096)
 };
@@ -42,7 +42,7 @@ cudaError_t launch_geometry(const double* theta, int64_t n, ParticleParams* out,
                             const double* sigma2_scaled, int n_det, double f_star, double df,
                             cudaStream_t s);
 
-// Pass A for particles [p0, p0 + np): writes the intermediate [np][D][N2][N1].
+// Pass A for particles [p0, p0 + np): writes the intermediate [np][2][N2][N1].
 template <typename Real>
 cudaError_t launch_pass_a(const FitnessPlan& plan, const ParticleParams* params, int64_t p0, int64_t np,
                           void* inter, cudaStream_t s);
@@ -54,8 +54,9 @@ cudaError_t launch_pass_b(const FitnessPlan& plan, const ParticleParams* params,
 cudaError_t launch_reduce(const Partial* partials, int64_t nb, const ParticleParams* params, int64_t p0,
                           int64_t np, double* fitness, int64_t* tc, cudaStream_t s);
 
-int pass_b_blocks_per_particle(int log_n1, int log_n2);
-int pass_a_k1b_for(int log_n2);
+int pass_b_blocks_per_particle(int log_n1, int log_n2, int precision);
+int pass_a_k1b_for(int log_n2, int precision);
+cudaError_t launch_stage_tables(int log_l, double2* t64, float2* t32, cudaStream_t s);
 
 // ---- create path (fcas_create.cu) ----
 cudaError_t launch_tables(int log_n, int log_n1, int log_n2, double2* tw64, double2* twlo64, double2* twhi64,

@@ -72,8 +72,7 @@ extern "C" int fcas_fitness_noalloc(const fcas_ctx* c, int64_t n, const double* 
     if (rc != FCAS_OK) return rc;
 
     const bool fp32 = c->setup.precision == FCAS_PREC_FP32;
-    const size_t csz = fp32 ? sizeof(float2) : sizeof(double2);
-    const size_t inter_pp = csz * (size_t)c->setup.n_det * (size_t)c->setup.n_fft;
+    const size_t inter_pp = inter_bytes_per_particle(c->setup.precision, c->setup.n_fft);
     const size_t part_pp = sizeof(Partial) * (size_t)c->nb_partials;
     const size_t per_particle = sizeof(ParticleParams) + part_pp + inter_pp;
     const size_t usable = kStaticScratchBytes - 3 * 256;

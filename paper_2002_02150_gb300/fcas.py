@@ -40,7 +40,8 @@ class fcas_info(ctypes.Structure):
     _fields_ = [("n_fft", ctypes.c_int64), ("n1", ctypes.c_int64), ("n2", ctypes.c_int64),
                 ("k_lo", ctypes.c_int64), ("k_hi", ctypes.c_int64), ("n_band", ctypes.c_int64),
                 ("chunk", ctypes.c_int64), ("n_det", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("scale", ctypes.c_double), ("sigma2", ctypes.c_double * FCAS_MAX_DET)]
+                ("scale", ctypes.c_double), ("sigma2", ctypes.c_double * FCAS_MAX_DET),
+                ("inter_bytes", ctypes.c_int64), ("series", ctypes.c_int64)]
 
 
 _lib = None

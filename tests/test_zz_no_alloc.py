@@ -48,14 +48,14 @@ def test_noalloc_matches_fitness_small(precision):
 
 
 def test_noalloc_matches_fitness_64s_segment_in_chunks():
-    # 4 det x 2^16 in FP32 needs 2 MiB of scratch per particle: 40 particles take several chunks
+    # 2^16 points in FP32 need 1 MiB of scratch per particle: 40 particles take two chunks
     _compare(sd.C1, "fp32", 40)
 
 
 def test_noalloc_rejects_oversized_segment_and_host_arrays():
     import torch
     import paper_2002_02150_gb300 as fc
-    w = dataclasses.replace(sd.SMALL, n_fft=1 << 20, n_samples=1 << 20, fs=4096.0, f_low=100.0, f_high=300.0)
+    w = dataclasses.replace(sd.SMALL, n_fft=1 << 21, n_samples=1 << 21, fs=4096.0, f_low=100.0, f_high=300.0)
     data = sd.make_dataset(w, 1, inject=False)
     theta = torch.tensor(sd.make_particles(w, 2, seed=1), device="cuda:0")
     f = torch.empty(2, dtype=torch.float64, device="cuda:0")
