@@ -1,5 +1,6 @@
 """Build libfcas.so in-tree with nvcc for sm_103a (one translation unit per process, then link)."""
 
+import hashlib
 import os
 import shutil
 import subprocess
@@ -24,9 +25,9 @@ def _nvcc():
     return exe
 
 
-def _compile(src, verbose):
-    obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
-    cmd = [_nvcc(), *FLAGS, *ARCH, "-c", os.path.join(CSRC, src), "-o", obj]
+def _compile(src, verbose, defines=(), build_dir=BUILD):
+    obj = os.path.join(build_dir, os.path.splitext(src)[0] + ".o")
+    cmd = [_nvcc(), *FLAGS, *ARCH, *[f"-D{d}" for d in defines], "-c", os.path.join(CSRC, src), "-o", obj]
     if verbose:
         print(" ".join(cmd), flush=True)
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -35,8 +36,21 @@ def _compile(src, verbose):
     return obj
 
 
-def build(verbose=False, force=False):
-    """Compile every CUDA source and link libfcas.so next to this file. Returns the library path."""
+def build(verbose=False, force=False, defines=(), out=None):
+    """Compile every CUDA source and link libfcas.so next to this file (or at `out`, with extra
+    preprocessor `defines` for launch-shape tuning). Returns the library path."""
+    if defines or out:
+        build_dir = BUILD + "_" + hashlib.sha1(" ".join(defines).encode()).hexdigest()[:8]
+        os.makedirs(build_dir, exist_ok=True)
+        with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+            objs = list(ex.map(lambda s: _compile(s, verbose, defines, build_dir), SOURCES))
+        target = out or LIB
+        r = subprocess.run([_nvcc(), *ARCH, "-shared", "-o", target + ".tmp", *objs, "-lcudart"], capture_output=True,
+                           text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+        os.replace(target + ".tmp", target)
+        return target
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
     headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".cuh", ".h"))]
     headers.append(os.path.join(HERE, "..", "include", "fcas.h"))

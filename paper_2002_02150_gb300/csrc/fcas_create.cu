@@ -218,7 +218,7 @@ cudaError_t launch_data_fft(const double* data, int n_det, int64_t n_samples, in
 
 // ------------------------------------------------------------------------------------------
 // Y_i[k] = s 4 df f_k^{-7/6} e^{-i pi/4} dt X~_i[k] / S_i[k] on the band (zero elsewhere), laid out
-// as [k1 / K1B][k2 < N2/2][k1 % K1B][i] with k = k1 + N1 k2 (the detectors of one bin adjacent),
+// as [k1 / K1B][i][k2 < N2/2][k1 % K1B] with k = k1 + N1 k2 (one detector's rows of a block adjacent),
 // and the float-float chirp basis phi^-5/3, phi^-1, phi^-2/3, phi^-1/3 (phi = f_k / f_*) in the
 // order [k1 / K1B][k2][k1 % K1B].
 // ------------------------------------------------------------------------------------------
@@ -248,8 +248,10 @@ __global__ void prep_kernel(const double2* __restrict__ spec, const double* __re
                 // (x.re + i x.im) (1 - i) / sqrt 2
                 yv = make_double2(a * rs2 * (x.x + x.y), a * rs2 * (x.y - x.x));
             }
-            if (precision == FCAS_PREC_FP32) static_cast<float2*>(y)[g * n_det + i] = make_float2((float)yv.x, (float)yv.y);
-            else static_cast<double2*>(y)[g * n_det + i] = yv;
+            // detector-major inside each block of K1B columns: [blk][i][k2][c]
+            const int64_t yi = ((blk * n_det + i) * half2 + k2) * k1b + c;
+            if (precision == FCAS_PREC_FP32) static_cast<float2*>(y)[yi] = make_float2((float)yv.x, (float)yv.y);
+            else static_cast<double2*>(y)[yi] = yv;
         }
         double b53 = 0.0, b1 = 0.0, b23 = 0.0, b13 = 0.0;
         if (in_band) {

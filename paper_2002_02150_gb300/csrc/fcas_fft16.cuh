@@ -147,8 +147,15 @@ __device__ __forceinline__ void fft16_stage(cplx<Real> (&v)[fft16_v(LOG_L)], cpl
     constexpr bool FIRST = DONE == 0;
     constexpr bool LAST = DONE + RB == LOG_L;
     if constexpr (!FIRST) {
+        if constexpr (G % 16 == 0) {
+            // pad(j + q G) = pad(j) + q (G + G/16): one base address, constant offsets
+            const C* rb = buf + fft16_pad(j) * es;
 #pragma unroll
-        for (int q = 0; q < V; ++q) v[q] = buf[fft16_pad(j + q * G) * es];
+            for (int q = 0; q < V; ++q) v[q] = rb[q * (G + G / 16) * es];
+        } else {
+#pragma unroll
+            for (int q = 0; q < V; ++q) v[q] = buf[fft16_pad(j + q * G) * es];
+        }
     }
 #pragma unroll
     for (int h = 0; h < T; ++h) {
@@ -200,8 +207,16 @@ __device__ __forceinline__ void fft16_stage(cplx<Real> (&v)[fft16_v(LOG_L)], cpl
         for (int h = 0; h < T; ++h) {
             const int jj = j + h * G;
             const int dst = (jj / NS) * NS * R + (jj & (NS - 1));
+            if constexpr ((NS == 1 && R == 16) || NS % 16 == 0) {
+                // pad(dst + r NS) = pad(dst) + r (NS + NS/16), or + r when NS = 1 and R = 16
+                constexpr int STRIDE = NS == 1 ? 1 : NS + NS / 16;
+                C* wb = buf + fft16_pad(dst) * es;
 #pragma unroll
-            for (int r = 0; r < R; ++r) buf[fft16_pad(dst + r * NS) * es] = v[h + r * T];
+                for (int r = 0; r < R; ++r) wb[r * STRIDE * es] = v[h + r * T];
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) buf[fft16_pad(dst + r * NS) * es] = v[h + r * T];
+            }
         }
         __syncthreads();
     }

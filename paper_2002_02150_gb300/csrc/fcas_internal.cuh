@@ -72,16 +72,27 @@ struct ParticleParams {
 // ------------------------------------------------------------------------------------------
 __host__ __device__ constexpr int imin_c(int a, int b) { return a < b ? a : b; }
 __host__ __device__ constexpr int imax_c(int a, int b) { return a > b ? a : b; }
+#ifndef FCAS_PASS_A_THREADS_F32
+#define FCAS_PASS_A_THREADS_F32 512   // target CTA size of pass A, FP32 form
+#endif
+#ifndef FCAS_PASS_A_SUB
+#define FCAS_PASS_A_SUB 8             // adjacent column blocks of one particle scheduled together
+#endif
+#ifndef FCAS_PASS_B_THREADS_F32
+#define FCAS_PASS_B_THREADS_F32 256   // target CTA size of pass B, FP32 form
+#endif
 __host__ __device__ constexpr int shape_v(int log_l) { return log_l >= 4 ? 16 : (1 << log_l); }
 __host__ __device__ constexpr int pass_a_k1b(int log_l, int real_bytes) {
-    return imin_c(imin_c(16, imax_c(1, (real_bytes == 4 ? 512 : 256) / ((1 << log_l) / shape_v(log_l)))),
+    return imin_c(imin_c(16, imax_c(1, (real_bytes == 4 ? FCAS_PASS_A_THREADS_F32 : 256) /
+                                           ((1 << log_l) / shape_v(log_l)))),
                   1 << log_l);
 }
 __host__ __device__ constexpr int pass_a_threads(int log_l, int real_bytes) {
     return pass_a_k1b(log_l, real_bytes) * ((1 << log_l) / shape_v(log_l));
 }
 __host__ __device__ constexpr int pass_b_tb(int log_l, int real_bytes) {
-    return imin_c(imin_c(16, imax_c(1, (real_bytes == 4 ? 256 : 128) / ((1 << log_l) / shape_v(log_l)))),
+    return imin_c(imin_c(16, imax_c(1, (real_bytes == 4 ? FCAS_PASS_B_THREADS_F32 : 128) /
+                                           ((1 << log_l) / shape_v(log_l)))),
                   (1 << log_l) / 2);
 }
 __host__ __device__ constexpr int pass_b_threads(int log_l, int real_bytes) {

@@ -29,7 +29,7 @@ struct FitnessPlan {
     int n_det;
     int log_n, log_n1, log_n2;
     int64_t n_samples;
-    const void* y;                // Y layout [k1 / K1B][k2 < N2/2][k1 % K1B][i]
+    const void* y;                // Y layout [k1 / K1B][i][k2 < N2/2][k1 % K1B]
     const void* basis;            // basis layout [k1 / K1B][k2 < N2/2][k1 % K1B]
     const void* stw_a;            // per-stage twiddles of the length-N2 transforms
     const void* stw_b;            // per-stage twiddles of the length-N1 transforms
