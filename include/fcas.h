@@ -134,6 +134,71 @@ int fcas_fitness(fcas_ctx* ctx, int64_t n, const double* theta, double* fitness,
 int fcas_fitness_noalloc(const fcas_ctx* ctx, int64_t n, const double* theta, double* fitness, int64_t* tc,
                          void* stream);
 
+/*
+ * Particle swarm optimisation (Sec. III): lbest PSO on a ring of particle indices, a fixed number of
+ * iterations, best-of-M independent runs with independent random streams. Details the paper defers
+ * to earlier work, as implemented here:
+ *  - positions normalised to [0,1]^4 and mapped linearly onto the box (alpha, delta, tau0, tau1.5);
+ *  - inertia w falls linearly from w_start to w_end over the iterations; every velocity component
+ *    is clamped to [-vmax, vmax];
+ *  - the neighbourhood of particle p is p and n_neighbours particles on each side (ring); its local
+ *    best is the best personal best there (lowest index on ties);
+ *  - a particle outside the box is not evaluated (its fitness counts as -inf: "let them fly");
+ *  - x0 ~ U[0,1]^4, v0 = clamp(u' - x0) with u' ~ U[0,1]^4;
+ *  - one iteration = evaluate, update personal bests, update local bests, move:
+ *      v <- clamp(((w v + (c1 r1)(pbest - x)) + (c2 r2)(lbest - x))),  x <- x + v
+ *    in binary64, in this order, without fused multiply-adds (bitwise reproducible);
+ *  - random numbers: Philox4x32-10 (Salmon et al., SC'11) keyed by the 64-bit seed, counter
+ *    (run, iteration, particle, stream) with stream 0 -> r1 / x0, 1 -> r2 / u'; the initial draws
+ *    use iteration 0xFFFFFFFF; uniforms are (u + 1/2) 2^-32.
+ */
+typedef struct fcas_pso_config {
+    int32_t n_runs;         /* independent runs, >= 1 */
+    int32_t n_particles;    /* particles per run, 1..1024 (the paper uses 40) */
+    int32_t n_iter;         /* iterations per run, >= 1 */
+    int32_t n_neighbours;   /* ring neighbours on each side, >= 0 (1: two neighbours, as in the paper) */
+    uint64_t seed;          /* Philox key */
+    double box[8];          /* alpha lo, hi, delta lo, hi [rad], tau0 lo, hi, tau1.5 lo, hi [s] */
+    double w_start, w_end;  /* inertia schedule */
+    double c1, c2;          /* cognitive and social weights */
+    double vmax;            /* velocity clamp (normalised units) */
+} fcas_pso_config;
+
+/* Device arrays of the swarm state, rows ordered run-major ([run * n_particles + p]). */
+typedef struct fcas_pso_state {
+    double* x;              /* [rows][4] normalised positions */
+    double* v;              /* [rows][4] velocities */
+    double* pbest_x;        /* [rows][4] personal-best positions */
+    double* pbest_f;        /* [rows] personal-best fitness (-inf before the first evaluation) */
+    int64_t* pbest_tc;      /* [rows] t_c sample index at the personal best (-1 if none) */
+} fcas_pso_state;
+
+typedef struct fcas_search_result {
+    double fitness;         /* best Gamma^2 of the run (its largest personal best) */
+    double theta[4];        /* where: (alpha, delta, tau0, tau1.5) */
+    int64_t tc;             /* its argmax t_c sample index */
+    int64_t evaluations;    /* fitness evaluations the run performed (particles inside the box) */
+} fcas_search_result;
+
+/* Initial positions, velocities and empty personal bests of every run (device state). Asynchronous. */
+int fcas_pso_init(const fcas_pso_config* cfg, const fcas_pso_state* state, void* stream);
+
+/*
+ * One PSO iteration `iter` (0-based) given the fitness and tc of the current positions
+ * (device arrays [rows]; entries of particles outside the box are ignored): personal bests, local
+ * bests, then the move. Asynchronous.
+ */
+int fcas_pso_update(const fcas_pso_config* cfg, int32_t iter, const double* fitness, const int64_t* tc,
+                    const fcas_pso_state* state, void* stream);
+
+/*
+ * fcas_search -- the full search on the context's data: n_runs x n_particles particles evolve
+ * together on the device for n_iter iterations; every iteration (positions -> parameters,
+ * fitness, update) is one CUDA-graph launch with no host round trip. results: host array
+ * [n_runs]. Synchronous.
+ */
+int fcas_search(fcas_ctx* ctx, const fcas_pso_config* cfg, fcas_search_result* results, void* stream);
+
 /* Release every resource held by the context (NULL is a no-op). Synchronises the device. */
 void fcas_destroy(fcas_ctx* ctx);
 

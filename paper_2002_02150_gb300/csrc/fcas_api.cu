@@ -9,6 +9,7 @@
 
 #include "fcas_ctx.cuh"
 #include "fcas_kernels.cuh"
+#include "fcas_pso.cuh"
 
 using namespace fcas;
 
@@ -57,9 +58,10 @@ namespace {
 void free_ctx(fcas_ctx* c) {
     void* ptrs[] = {c->d_det, c->d_sigma2s, c->d_y, c->d_basis, c->d_tw64, c->d_twlo64, c->d_twhi64,
                     c->d_tw32, c->d_twlo32, c->d_twhi32, c->d_stw_a64, c->d_stw_a32, c->d_stw_b64, c->d_stw_b32,
-                    c->d_params, c->d_theta, c->d_fit, c->d_tc, c->d_inter, c->d_partials};
+                    c->d_params, c->d_theta, c->d_fit, c->d_tc, c->d_inter, c->d_partials, c->d_pso};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    if (c->search_stream) cudaStreamDestroy(c->search_stream);
     for (auto& e : c->events) {
         cudaEventDestroy(e.a);
         cudaEventDestroy(e.b);
@@ -134,6 +136,33 @@ void prof_begin(fcas_ctx* c, int kind, cudaStream_t s, size_t* slot) {
 void prof_end(fcas_ctx* c, size_t slot, cudaStream_t s) {
     if (slot != SIZE_MAX) cudaEventRecord(c->events[slot].b, s);
 }
+
+// Passes A, B and the final argmax over chunks of the context's particle parameters.
+cudaError_t launch_passes(fcas_ctx* c, int64_t n, double* d_fit, int64_t* d_tc, cudaStream_t st) {
+    const FitnessPlan plan = make_plan(c);
+    const bool fp32 = c->setup.precision == FCAS_PREC_FP32;
+    size_t slot;
+    cudaError_t e = cudaSuccess;
+    for (int64_t p0 = 0; p0 < n && e == cudaSuccess; p0 += c->chunk) {
+        const int64_t np = (n - p0) < c->chunk ? (n - p0) : c->chunk;
+        prof_begin(c, FCAS_KERNEL_PASS_A, st, &slot);
+        e = fp32 ? launch_pass_a<float>(plan, c->d_params, p0, np, c->d_inter, st)
+                 : launch_pass_a<double>(plan, c->d_params, p0, np, c->d_inter, st);
+        prof_end(c, slot, st);
+        if (e != cudaSuccess) break;
+        prof_begin(c, FCAS_KERNEL_PASS_B, st, &slot);
+        e = fp32 ? launch_pass_b<float>(plan, c->d_params, p0, np, c->d_inter, c->d_partials, st)
+                 : launch_pass_b<double>(plan, c->d_params, p0, np, c->d_inter, c->d_partials, st);
+        prof_end(c, slot, st);
+        if (e != cudaSuccess) break;
+        prof_begin(c, FCAS_KERNEL_REDUCE, st, &slot);
+        e = launch_reduce(c->d_partials, c->nb_partials, c->d_params, p0, np, d_fit, d_tc, st);
+        prof_end(c, slot, st);
+    }
+    return e;
+}
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
 }  // namespace
 
@@ -365,25 +394,98 @@ int fcas_fitness(fcas_ctx* c, int64_t n, const double* theta, double* fitness, i
     FCAS_CUDA(launch_geometry(d_theta, n, c->d_params, c->d_det, c->d_sigma2s, c->setup.n_det, c->setup.f_low, c->df,
                               st));
     prof_end(c, slot, st);
-    const FitnessPlan plan = make_plan(c);
-    const bool fp32 = c->setup.precision == FCAS_PREC_FP32;
-    for (int64_t p0 = 0; p0 < n; p0 += c->chunk) {
-        const int64_t np = (n - p0) < c->chunk ? (n - p0) : c->chunk;
-        prof_begin(c, FCAS_KERNEL_PASS_A, st, &slot);
-        FCAS_CUDA(fp32 ? launch_pass_a<float>(plan, c->d_params, p0, np, c->d_inter, st)
-                       : launch_pass_a<double>(plan, c->d_params, p0, np, c->d_inter, st));
-        prof_end(c, slot, st);
-        prof_begin(c, FCAS_KERNEL_PASS_B, st, &slot);
-        FCAS_CUDA(fp32 ? launch_pass_b<float>(plan, c->d_params, p0, np, c->d_inter, c->d_partials, st)
-                       : launch_pass_b<double>(plan, c->d_params, p0, np, c->d_inter, c->d_partials, st));
-        prof_end(c, slot, st);
-        prof_begin(c, FCAS_KERNEL_REDUCE, st, &slot);
-        FCAS_CUDA(launch_reduce(c->d_partials, c->nb_partials, c->d_params, p0, np, d_fit, d_tc, st));
-        prof_end(c, slot, st);
-    }
+    FCAS_CUDA(launch_passes(c, n, d_fit, d_tc, st));
     if (!f_dev) FCAS_CUDA(cudaMemcpyAsync(fitness, d_fit, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, st));
     if (!t_dev) FCAS_CUDA(cudaMemcpyAsync(tc, d_tc, sizeof(int64_t) * (size_t)n, cudaMemcpyDeviceToHost, st));
     if (!th_dev || !f_dev || !t_dev) FCAS_CUDA(cudaStreamSynchronize(st));
+    return FCAS_OK;
+}
+
+int fcas_search(fcas_ctx* c, const fcas_pso_config* cfg, fcas_search_result* results, void* stream) {
+    g_last_error.clear();
+    if (!c || !results) return fail(FCAS_ERR_INVALID, "fcas_search: NULL argument");
+    char msg[256];
+    int rc = pso_validate(cfg, msg, sizeof(msg));
+    if (rc) return fail(rc, "fcas_search: %s", msg);
+    const int64_t rows = (int64_t)cfg->n_runs * cfg->n_particles;
+    rc = ensure_particles(c, rows);
+    if (rc) return rc;
+    // one allocation: x, v, pbest_x, theta [rows][4]; pbest_f, fitness [rows]; pbest_tc, tc [rows];
+    // iteration and evaluation counters [runs]; results [runs]
+    const size_t r4 = align256(sizeof(double) * 4 * rows), r1 = align256(sizeof(double) * rows);
+    const size_t ri = align256(sizeof(int64_t) * rows);
+    const size_t need = 4 * r4 + 2 * r1 + 2 * ri + align256(sizeof(int32_t) * cfg->n_runs) +
+                        align256(sizeof(int64_t) * cfg->n_runs) + align256(sizeof(fcas_search_result) * cfg->n_runs);
+    if (need > c->pso_bytes) {
+        if (c->d_pso) cudaFree(c->d_pso);
+        c->d_pso = nullptr;
+        c->pso_bytes = 0;
+        rc = dev_alloc(&c->d_pso, need, "swarm state");
+        if (rc) return rc;
+        c->pso_bytes = need;
+    }
+    unsigned char* b = c->d_pso;
+    PsoStateDev s;
+    s.x = reinterpret_cast<double*>(b);
+    s.v = reinterpret_cast<double*>(b + r4);
+    s.pbest_x = reinterpret_cast<double*>(b + 2 * r4);
+    double* theta = reinterpret_cast<double*>(b + 3 * r4);
+    s.pbest_f = reinterpret_cast<double*>(b + 4 * r4);
+    double* fit = reinterpret_cast<double*>(b + 4 * r4 + r1);
+    s.pbest_tc = reinterpret_cast<int64_t*>(b + 4 * r4 + 2 * r1);
+    int64_t* tcs = reinterpret_cast<int64_t*>(b + 4 * r4 + 2 * r1 + ri);
+    size_t off = 4 * r4 + 2 * r1 + 2 * ri;
+    s.iter = reinterpret_cast<int32_t*>(b + off);
+    off += align256(sizeof(int32_t) * cfg->n_runs);
+    s.evals = reinterpret_cast<int64_t*>(b + off);
+    off += align256(sizeof(int64_t) * cfg->n_runs);
+    fcas_search_result* d_res = reinterpret_cast<fcas_search_result*>(b + off);
+
+    if (!c->search_stream) FCAS_CUDA(cudaStreamCreateWithFlags(&c->search_stream, cudaStreamNonBlocking));
+    cudaStream_t st = c->search_stream;
+    cudaStream_t user = static_cast<cudaStream_t>(stream);
+    cudaEvent_t ev;
+    FCAS_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    cudaEventRecord(ev, user);
+    cudaStreamWaitEvent(st, ev, 0);
+    const PsoDev g = pso_dev(cfg);
+    const bool prof = c->prof;
+    c->prof = false;
+    cudaError_t e = launch_pso_init(g, s, st);
+    // one iteration: parameters of the particles inside the box, their fitness, the swarm update
+    auto iteration = [&]() -> cudaError_t {
+        cudaError_t x = launch_pso_theta(g, s, theta, st);
+        if (x == cudaSuccess)
+            x = launch_geometry(theta, rows, c->d_params, c->d_det, c->d_sigma2s, c->setup.n_det, c->setup.f_low,
+                                c->df, st);
+        if (x == cudaSuccess) x = launch_passes(c, rows, fit, tcs, st);
+        if (x == cudaSuccess) x = launch_pso_update(g, 0, fit, tcs, s, st);
+        return x;
+    };
+    // the first iteration runs eagerly (it also sets the kernels' shared-memory attributes);
+    // the others replay a graph of it
+    if (e == cudaSuccess) e = iteration();
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    if (e == cudaSuccess && cfg->n_iter > 1) {
+        e = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed);
+        if (e == cudaSuccess) {
+            cudaError_t ei = iteration();
+            e = cudaStreamEndCapture(st, &graph);
+            if (e == cudaSuccess) e = ei;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        for (int it = 1; it < cfg->n_iter && e == cudaSuccess; ++it) e = cudaGraphLaunch(exec, st);
+    }
+    if (e == cudaSuccess) e = launch_pso_result(g, s, d_res, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(results, d_res, sizeof(fcas_search_result) * cfg->n_runs, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    cudaEventDestroy(ev);
+    c->prof = prof;
+    if (e != cudaSuccess) return fail(FCAS_ERR_CUDA, "fcas_search: %s", cudaGetErrorString(e));
     return FCAS_OK;
 }
 

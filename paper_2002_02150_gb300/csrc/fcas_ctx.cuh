@@ -56,6 +56,10 @@ struct fcas_ctx {
     fcas::Partial* d_partials = nullptr;  // [chunk][blocks per particle]
     int64_t chunk = 0;
     int64_t nb_partials = 0;
+    // particle swarm search
+    unsigned char* d_pso = nullptr;  // state, parameters, fitness, counters and results of the swarm
+    size_t pso_bytes = 0;
+    cudaStream_t search_stream = nullptr;
     // profiling
     bool prof = false;
     std::vector<fcas::EventPair> events;

@@ -212,6 +212,7 @@ pass_a_kernel(const cplx<Real>* __restrict__ y, const Basis<Real>* __restrict__ 
     const int blk = (int)((rest / np) * sub + lin % sub);
     const int k1 = blk * K1B + c;
     const ParticleParams* pp = params + p0 + p;
+    if (!pp->valid) return;   // not evaluated (invalid input, or a PSO particle outside its box)
     if (threadIdx.x < FCAS_MAX_DET) {
         const int i = threadIdx.x;
         if constexpr (sizeof(Real) == 4) {
@@ -326,8 +327,8 @@ __device__ __forceinline__ bool better_f(float v, int t, float bv, int bt) {
 
 template <typename Real, int LOG_L>
 __global__ void __launch_bounds__(pass_b_threads(LOG_L, sizeof(Real)), 2)
-pass_b_kernel(const cplx<Real>* __restrict__ inter, int log_n2, int64_t n_samples,
-              const cplx<Real>* __restrict__ stw, Partial* __restrict__ partials) {
+pass_b_kernel(const cplx<Real>* __restrict__ inter, const ParticleParams* __restrict__ params, int64_t p0,
+              int log_n2, int64_t n_samples, const cplx<Real>* __restrict__ stw, Partial* __restrict__ partials) {
     using C = cplx<Real>;
     constexpr int L = 1 << LOG_L;
     constexpr int V = shape_v(LOG_L);
@@ -346,6 +347,7 @@ pass_b_kernel(const cplx<Real>* __restrict__ inter, int log_n2, int64_t n_sample
     const int n2 = 1 << log_n2;
     const int ta = blockIdx.x * TB + c;
     const int64_t p = blockIdx.y;
+    if (!params[p0 + p].valid) return;   // the final reduce reports NaN for it
 
     Real g[V];
 #pragma unroll
@@ -485,8 +487,8 @@ static cudaError_t pass_a_at(const FitnessPlan& pl, const ParticleParams* params
 }
 
 template <typename Real, int LG>
-static cudaError_t pass_b_at(const FitnessPlan& pl, int64_t np, const void* inter, Partial* partials,
-                             cudaStream_t s) {
+static cudaError_t pass_b_at(const FitnessPlan& pl, const ParticleParams* params, int64_t p0, int64_t np,
+                             const void* inter, Partial* partials, cudaStream_t s) {
     constexpr int TB = pass_b_tb(LG, sizeof(Real));
     constexpr int THREADS = pass_b_threads(LG, sizeof(Real));
     const size_t smem = sizeof(cplx<Real>) * (size_t)TB * fft16_buf_elems(LG);
@@ -494,7 +496,7 @@ static cudaError_t pass_b_at(const FitnessPlan& pl, int64_t np, const void* inte
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((1 << pl.log_n2) / TB), (unsigned)np);
-    kern<<<grid, THREADS, smem, s>>>(static_cast<const cplx<Real>*>(inter), pl.log_n2, pl.n_samples,
+    kern<<<grid, THREADS, smem, s>>>(static_cast<const cplx<Real>*>(inter), params, p0, pl.log_n2, pl.n_samples,
                                      static_cast<const cplx<Real>*>(pl.stw_b), partials);
     return cudaGetLastError();
 }
@@ -514,11 +516,9 @@ cudaError_t launch_pass_a(const FitnessPlan& pl, const ParticleParams* params, i
 template <typename Real>
 cudaError_t launch_pass_b(const FitnessPlan& pl, const ParticleParams* params, int64_t p0, int64_t np,
                           const void* inter, Partial* partials, cudaStream_t s) {
-    (void)params;
-    (void)p0;
     if (np <= 0) return cudaSuccess;
     switch (pl.log_n1) {
-#define FCAS_CASE(LG) case LG: return pass_b_at<Real, LG>(pl, np, inter, partials, s);
+#define FCAS_CASE(LG) case LG: return pass_b_at<Real, LG>(pl, params, p0, np, inter, partials, s);
         FCAS_LOG_CASES(FCAS_CASE)
 #undef FCAS_CASE
         default: return cudaErrorInvalidValue;

@@ -44,6 +44,23 @@ class fcas_info(ctypes.Structure):
                 ("inter_bytes", ctypes.c_int64), ("series", ctypes.c_int64)]
 
 
+class fcas_pso_config(ctypes.Structure):
+    _fields_ = [("n_runs", ctypes.c_int32), ("n_particles", ctypes.c_int32), ("n_iter", ctypes.c_int32),
+                ("n_neighbours", ctypes.c_int32), ("seed", ctypes.c_uint64), ("box", ctypes.c_double * 8),
+                ("w_start", ctypes.c_double), ("w_end", ctypes.c_double), ("c1", ctypes.c_double),
+                ("c2", ctypes.c_double), ("vmax", ctypes.c_double)]
+
+
+class fcas_pso_state(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_void_p), ("v", ctypes.c_void_p), ("pbest_x", ctypes.c_void_p),
+                ("pbest_f", ctypes.c_void_p), ("pbest_tc", ctypes.c_void_p)]
+
+
+class fcas_search_result(ctypes.Structure):
+    _fields_ = [("fitness", ctypes.c_double), ("theta", ctypes.c_double * 4), ("tc", ctypes.c_int64),
+                ("evaluations", ctypes.c_int64)]
+
+
 _lib = None
 
 
@@ -76,6 +93,13 @@ def load_library():
     lib.fcas_profile_enable.restype = i32
     lib.fcas_profile_read.argtypes = [vp, i32, ctypes.POINTER(dp), ctypes.POINTER(i64)]
     lib.fcas_profile_read.restype = i32
+    lib.fcas_pso_init.argtypes = [ctypes.POINTER(fcas_pso_config), ctypes.POINTER(fcas_pso_state), vp]
+    lib.fcas_pso_init.restype = i32
+    lib.fcas_pso_update.argtypes = [ctypes.POINTER(fcas_pso_config), ctypes.c_int32, vp, vp,
+                                    ctypes.POINTER(fcas_pso_state), vp]
+    lib.fcas_pso_update.restype = i32
+    lib.fcas_search.argtypes = [vp, ctypes.POINTER(fcas_pso_config), ctypes.POINTER(fcas_search_result), vp]
+    lib.fcas_search.restype = i32
     _lib = lib
     return lib
 
@@ -218,3 +242,38 @@ def fcas_profile_read(ctx, kind):
     k = KERNEL_KINDS[kind] if isinstance(kind, str) else int(kind)
     _check(load_library().fcas_profile_read(ctx.handle, k, ctypes.byref(total), ctypes.byref(launches)))
     return total.value, launches.value
+
+
+def pso_config(n_runs=8, n_particles=40, n_iter=2000, n_neighbours=1, seed=0, box=None, w_start=0.9, w_end=0.4,
+               c1=2.0, c2=2.0, vmax=0.5):
+    """fcas_pso_config; box = (alpha lo, hi, delta lo, hi, tau0 lo, hi, tau1.5 lo, hi)."""
+    cfg = fcas_pso_config()
+    cfg.n_runs, cfg.n_particles, cfg.n_iter, cfg.n_neighbours = n_runs, n_particles, n_iter, n_neighbours
+    cfg.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    cfg.box[:] = [float(b) for b in box]
+    cfg.w_start, cfg.w_end, cfg.c1, cfg.c2, cfg.vmax = w_start, w_end, c1, c2, vmax
+    return cfg
+
+
+def _state(x, v, pbest_x, pbest_f, pbest_tc):
+    return fcas_pso_state(*(ctypes.c_void_p(t.data_ptr()) for t in (x, v, pbest_x, pbest_f, pbest_tc)))
+
+
+def fcas_pso_init(cfg, x, v, pbest_x, pbest_f, pbest_tc, stream=None):
+    """Initialise device state tensors (torch CUDA, float64 / int64, rows = n_runs * n_particles)."""
+    st = _state(x, v, pbest_x, pbest_f, pbest_tc)
+    _check(load_library().fcas_pso_init(ctypes.byref(cfg), ctypes.byref(st), _stream(stream, x)))
+
+
+def fcas_pso_update(cfg, it, fitness, tc, x, v, pbest_x, pbest_f, pbest_tc, stream=None):
+    st = _state(x, v, pbest_x, pbest_f, pbest_tc)
+    _check(load_library().fcas_pso_update(ctypes.byref(cfg), int(it), ctypes.c_void_p(fitness.data_ptr()),
+                                          ctypes.c_void_p(tc.data_ptr()), ctypes.byref(st), _stream(stream, x)))
+
+
+def fcas_search(ctx, cfg, stream=None):
+    """Run the device PSO search; returns a list of dicts (one per run)."""
+    res = (fcas_search_result * cfg.n_runs)()
+    s = ctypes.c_void_p(int(stream)) if stream is not None else ctypes.c_void_p(0)
+    _check(load_library().fcas_search(ctx.handle, ctypes.byref(cfg), res, s))
+    return [dict(fitness=r.fitness, theta=list(r.theta), tc=r.tc, evaluations=r.evaluations) for r in res]

@@ -41,14 +41,18 @@ def test_struct_layouts_match_header(tmp_path):
     import paper_2002_02150_gb300.fcas as f
     src = tmp_path / "layout.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "fcas.h"\n'
-                   'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(fcas_detector), sizeof(fcas_setup),'
-                   ' offsetof(fcas_setup, fs), offsetof(fcas_setup, max_batch), sizeof(fcas_info),'
-                   ' offsetof(fcas_info, sigma2)); return 0;}\n')
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(fcas_detector),'
+                   ' sizeof(fcas_setup), offsetof(fcas_setup, fs), offsetof(fcas_setup, max_batch),'
+                   ' sizeof(fcas_info), offsetof(fcas_info, sigma2), sizeof(fcas_pso_config),'
+                   ' offsetof(fcas_pso_config, box), offsetof(fcas_pso_config, vmax), sizeof(fcas_search_result),'
+                   ' sizeof(fcas_pso_state)); return 0;}\n')
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     expect = [ctypes.sizeof(f.fcas_detector), ctypes.sizeof(f.fcas_setup), f.fcas_setup.fs.offset,
-              f.fcas_setup.max_batch.offset, ctypes.sizeof(f.fcas_info), f.fcas_info.sigma2.offset]
+              f.fcas_setup.max_batch.offset, ctypes.sizeof(f.fcas_info), f.fcas_info.sigma2.offset,
+              ctypes.sizeof(f.fcas_pso_config), f.fcas_pso_config.box.offset, f.fcas_pso_config.vmax.offset,
+              ctypes.sizeof(f.fcas_search_result), ctypes.sizeof(f.fcas_pso_state)]
     assert got == expect
 
 
@@ -84,3 +88,20 @@ def test_null_arguments_are_rejected(lib):
     assert lib.fcas_fitness(None, 1, None, None, None, None) == -1
     lib.fcas_destroy(None)
     assert lib.fcas_version() >= 100
+
+
+def test_pso_config_validation(lib):
+    import paper_2002_02150_gb300.fcas as f
+    box = [0, 6.2, -1.5, 1.5, 1.0, 2.0, 0.1, 0.2]
+    st = f.fcas_pso_state()
+    for bad in (dict(n_particles=2000), dict(n_runs=0), dict(n_iter=0), dict(n_neighbours=-1)):
+        kw = dict(n_runs=2, n_particles=8, n_iter=5, box=box)
+        kw.update(bad)
+        cfg = f.pso_config(**kw)
+        assert lib.fcas_pso_init(ctypes.byref(cfg), ctypes.byref(st), None) == -1
+    cfg = f.pso_config(n_runs=2, n_particles=8, n_iter=5, box=[0, 6.2, -1.5, 1.5, 2.0, 1.0, 0.1, 0.2])
+    assert lib.fcas_pso_init(ctypes.byref(cfg), ctypes.byref(st), None) == -1
+    assert "lo < hi" in lib.fcas_last_error().decode()
+    cfg = f.pso_config(n_runs=2, n_particles=8, n_iter=5, box=box)
+    assert lib.fcas_pso_init(ctypes.byref(cfg), ctypes.byref(st), None) == -1     # NULL state arrays
+    assert lib.fcas_pso_update(ctypes.byref(cfg), 9, None, None, ctypes.byref(st), None) == -1

@@ -1,0 +1,113 @@
+"""GPU checks of the device lbest PSO (Sec. III) through the C ABI."""
+
+import dataclasses
+import math
+
+import numpy as np
+import pytest
+
+import synthdata as sd
+from oracle import fcas_oracle as o
+from oracle import pso_oracle as po
+from parity_util import RTOL, TIE_RTOL, make_ctx, oracle_setup
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2002_02150_gb300 import build as b
+    b.build()
+
+
+def _box(w):
+    t0lo, t0hi, t15lo, t15hi = sd.chirp_time_box(w.f_low)
+    return (0.0, 2 * math.pi, -0.5 * math.pi, 0.5 * math.pi, t0lo, t0hi, t15lo, t15hi)
+
+
+def _cfgs(w, **kw):
+    import paper_2002_02150_gb300 as fc
+    return po.PsoConfig(box=_box(w), **kw), fc.pso_config(box=_box(w), **kw)
+
+
+def test_device_update_reproduces_the_oracle_step_bit_for_bit():
+    import torch
+    import paper_2002_02150_gb300 as fc
+    w = sd.SMALL
+    data = sd.make_dataset(w, 0)
+    setup = oracle_setup(w, data)
+    ocfg, dcfg = _cfgs(w, n_runs=3, n_particles=12, n_iter=8, seed=99, n_neighbours=1)
+    rows = 36
+    dev = dict(device="cuda:0")
+    x = torch.empty((rows, 4), dtype=torch.float64, **dev)
+    v, pbx = torch.empty_like(x), torch.empty_like(x)
+    pbf = torch.empty(rows, dtype=torch.float64, **dev)
+    pbt = torch.empty(rows, dtype=torch.int64, **dev)
+    fc.fcas_pso_init(dcfg, x, v, pbx, pbf, pbt)
+    s = po.init_state(ocfg)
+
+    def check():
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(x.cpu().numpy(), s.x.reshape(-1, 4))
+        np.testing.assert_array_equal(v.cpu().numpy(), s.v.reshape(-1, 4))
+        np.testing.assert_array_equal(pbx.cpu().numpy(), s.pbest_x.reshape(-1, 4))
+        np.testing.assert_array_equal(pbf.cpu().numpy(), s.pbest_f.reshape(-1))
+        np.testing.assert_array_equal(pbt.cpu().numpy(), s.pbest_tc.reshape(-1))
+
+    check()
+    outside_seen = 0
+    for it in range(ocfg.n_iter):
+        flat = s.x.reshape(-1, 4)
+        inside = po.in_box(flat)
+        outside_seen += int((~inside).sum())
+        fit = np.full(rows, np.nan)        # outside the box: ignored by both sides
+        tcs = np.full(rows, -1, dtype=np.int64)
+        for r in np.nonzero(inside)[0]:
+            fit[r], tcs[r] = o.fitness(setup, po.to_theta(ocfg, flat[r]))
+        po.update(ocfg, s, it, fit.reshape(3, 12), tcs.reshape(3, 12))
+        fc.fcas_pso_update(dcfg, it, torch.tensor(fit, **dev), torch.tensor(tcs, **dev), x, v, pbx, pbf, pbt)
+        check()
+    assert outside_seen > 0      # the let-them-fly rule was exercised
+
+
+def test_search_reports_consistent_optimum():
+    import torch
+    import paper_2002_02150_gb300 as fc
+    w = sd.SMALL
+    data = sd.make_dataset(w, 1)
+    _, dcfg = _cfgs(w, n_runs=2, n_particles=24, n_iter=60, seed=5)
+    setup = oracle_setup(w, data)
+    with make_ctx(w, data, "fp32") as ctx:
+        res = fc.fcas_search(ctx, dcfg)
+        assert len(res) == 2
+        th = np.array([r["theta"] for r in res])
+        f, t = fc.fcas_fitness(ctx, torch.tensor(th, device="cuda:0"))
+        torch.cuda.synchronize()
+        f, t = f.cpu().numpy(), t.cpu().numpy()
+    for j, r in enumerate(res):
+        assert 0 < r["evaluations"] <= 60 * 24
+        assert r["fitness"] == pytest.approx(f[j], rel=1e-12) and r["tc"] == t[j]
+        curve = o.fitness_curve(setup, th[j])[: setup.n_samples]
+        g_ref = curve.max()
+        assert abs(r["fitness"] - g_ref) / g_ref <= RTOL["fp32"]
+        assert r["tc"] == int(np.argmax(curve)) or abs(curve[r["tc"]] - g_ref) / g_ref <= TIE_RTOL
+
+
+def test_search_recovers_a_noiseless_injection():
+    import paper_2002_02150_gb300 as fc
+    w = dataclasses.replace(sd.SMALL, n_samples=sd.SMALL.n_fft)
+    data = sd.make_dataset(w, 3, noise=False)
+    inj = data["inj"]
+    t0, _, t15, _ = o.chirp_times_from_masses(inj["m1"], inj["m2"], w.f_low)
+    box = (inj["alpha"] - 0.3, inj["alpha"] + 0.3, inj["delta"] - 0.3, inj["delta"] + 0.3,
+           0.97 * t0, 1.03 * t0, 0.97 * t15, 1.03 * t15)
+    cfg = fc.pso_config(n_runs=4, n_particles=32, n_iter=150, seed=11, box=box)
+    with make_ctx(w, data, "fp32") as ctx:
+        res = fc.fcas_search(ctx, cfg)
+    best = max(res, key=lambda r: r["fitness"])
+    assert best["fitness"] >= 0.95 * inj["snr"] ** 2
+    assert best["fitness"] <= inj["snr"] ** 2 * (1 + 1e-4)
+    assert abs(best["theta"][2] / t0 - 1) < 0.01
