@@ -199,6 +199,19 @@ int fcas_pso_update(const fcas_pso_config* cfg, int32_t iter, const double* fitn
  */
 int fcas_search(fcas_ctx* ctx, const fcas_pso_config* cfg, fcas_search_result* results, void* stream);
 
+/*
+ * fcas_gradient -- d Gamma^2 / d theta at a fixed t_c (the argmax returned by fcas_fitness:
+ * envelope theorem, the maximisation over t_c is held fixed), theta = (alpha, delta, tau0, tau1.5).
+ *   theta : [n][4] (host or device);  tc : [n] t_c sample index (host or device);
+ *   grad  : [n][4] (d/d alpha, d/d delta, d/d tau0, d/d tau1.5) of Gamma^2 [per rad, per s]
+ *           (host or device).
+ * The six band sums each detector needs at t_c (Z, sum k Q, and the four chirp-basis moments)
+ * are reduced in binary64; the per-particle combination (antenna patterns, delays, G^-1 and
+ * the chirp coefficients, differentiated analytically) is binary64. Particles with invalid input,
+ * tc < 0, or an ill-conditioned G (the rank-1 rule of fcas_fitness) get NaN.
+ */
+int fcas_gradient(fcas_ctx* ctx, int64_t n, const double* theta, const int64_t* tc, double* grad, void* stream);
+
 /* Release every resource held by the context (NULL is a no-op). Synchronises the device. */
 void fcas_destroy(fcas_ctx* ctx);
 

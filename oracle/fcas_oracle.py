@@ -244,3 +244,67 @@ def fitness_batch(setup, thetas):
     for j, th in enumerate(thetas):
         out_f[j], out_t[j] = fitness(setup, th)
     return out_f, out_t
+
+
+# --------------------------------------------------------------------------------------------
+# Gradient of Gamma^2 at a fixed t_c (envelope theorem: the argmax over t_c is held fixed)
+# --------------------------------------------------------------------------------------------
+
+def _statistic_at(setup, theta, t):
+    """Gamma^2(theta, t) at one t_c with only real-analytic operations (direct sums with cos and
+    sin, no FFT, no conjugation), so that it accepts complex theta for complex-step derivatives."""
+    alpha, delta, tau0, tau15 = theta
+    ca, sa, cd, sd = np.cos(alpha), np.sin(alpha), np.cos(delta), np.sin(delta)
+    n = np.array([cd * ca, cd * sa, sd])
+    bx = np.array([sa, -ca, 0.0 * sa])
+    by = np.array([-sd * ca, -sd * sa, cd])
+    f_star = setup.f_low
+    x = 5.0 * tau15 / (32.0 * math.pi * tau0)
+    eta = x ** (-2.0 / 3.0) / (8.0 * f_star * tau15)
+    tau1 = 5.0 / (192.0 * math.pi * f_star * eta * x) * (743.0 / 336.0 + 11.0 * eta / 4.0)
+    tau2 = 5.0 / (128.0 * math.pi * f_star * eta * x ** (1.0 / 3.0)) * (
+        3058673.0 / 1016064.0 + 5429.0 * eta / 1008.0 + 617.0 * eta ** 2 / 144.0)
+    phi = setup.f / f_star
+    psi_turns = (0.6 * f_star * tau0 * phi ** (-5.0 / 3.0) + f_star * tau1 / phi
+                 - 1.5 * f_star * tau15 * phi ** (-2.0 / 3.0) + 3.0 * f_star * tau2 * phi ** (-1.0 / 3.0))
+    amp = 4.0 * setup.df * setup.f ** (-7.0 / 6.0)
+    shift = (setup.k * t % setup.n_fft) / setup.n_fft          # e^{2 pi i k t / N}, exact turns
+    u = []
+    cs = []
+    ss = []
+    for i in range(setup.n_det):
+        xa, ya = setup.det[i, 3:6], setup.det[i, 6:9]
+        xX, xY, yX, yY = xa @ bx, xa @ by, ya @ bx, ya @ by
+        u.append((0.5 * (xX * xX - xY * xY - yX * yX + yY * yY), xX * xY - yX * yY))
+        delay = -(setup.det[i, 0:3] @ n) / C_LIGHT
+        # Q = 4 df y~ e^{2 pi i f Delta} h~_c*, h~_c* = f^-7/6 e^{i(psi - pi/4)}; times e^{2 pi i k t / N}
+        ph = 2.0 * math.pi * (psi_turns + setup.f * delay + shift) - math.pi / 4.0
+        yr, yi = np.real(setup.y[i]), np.imag(setup.y[i])
+        re = amp * (yr * np.cos(ph) - yi * np.sin(ph))
+        im = amp * (yr * np.sin(ph) + yi * np.cos(ph))
+        cs.append(np.sum(re))          # c_i = Re Z_i
+        ss.append(-np.sum(im))         # s_i = -Im Z_i
+    g11 = sum(setup.sigma2[i] * u[i][0] * u[i][0] for i in range(setup.n_det))
+    g12 = sum(setup.sigma2[i] * u[i][0] * u[i][1] for i in range(setup.n_det))
+    g22 = sum(setup.sigma2[i] * u[i][1] * u[i][1] for i in range(setup.n_det))
+    det = g11 * g22 - g12 * g12
+    xc = (sum(u[i][0] * cs[i] for i in range(setup.n_det)), sum(u[i][1] * cs[i] for i in range(setup.n_det)))
+    xs = (sum(u[i][0] * ss[i] for i in range(setup.n_det)), sum(u[i][1] * ss[i] for i in range(setup.n_det)))
+    quad = lambda v: (g22 * v[0] * v[0] - 2.0 * g12 * v[0] * v[1] + g11 * v[1] * v[1]) / det
+    return quad(xc) + quad(xs)
+
+
+def statistic_at(setup, theta, t):
+    """Gamma^2(theta, t) at a single t_c (real)."""
+    return float(np.real(_statistic_at(setup, [complex(v) for v in theta], int(t))))
+
+
+def gradient(setup, theta, t, h=1e-30):
+    """d Gamma^2(theta, t) / d theta at fixed t by the complex-step derivative
+    Im f(theta + i h e_j) / h (exact to rounding for a real-analytic f; full-rank G only)."""
+    g = np.empty(4)
+    for j in range(4):
+        th = [complex(v) for v in theta]
+        th[j] += 1j * h
+        g[j] = np.imag(_statistic_at(setup, th, int(t))) / h
+    return g

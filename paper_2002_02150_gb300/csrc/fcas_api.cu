@@ -58,7 +58,8 @@ namespace {
 void free_ctx(fcas_ctx* c) {
     void* ptrs[] = {c->d_det, c->d_sigma2s, c->d_y, c->d_basis, c->d_tw64, c->d_twlo64, c->d_twhi64,
                     c->d_tw32, c->d_twlo32, c->d_twhi32, c->d_stw_a64, c->d_stw_a32, c->d_stw_b64, c->d_stw_b32,
-                    c->d_params, c->d_theta, c->d_fit, c->d_tc, c->d_inter, c->d_partials, c->d_pso};
+                    c->d_params, c->d_theta, c->d_fit, c->d_tc, c->d_inter, c->d_partials, c->d_pso,
+                    c->d_gsums, c->d_gstage};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->search_stream) cudaStreamDestroy(c->search_stream);
@@ -486,6 +487,59 @@ int fcas_search(fcas_ctx* c, const fcas_pso_config* cfg, fcas_search_result* res
     cudaEventDestroy(ev);
     c->prof = prof;
     if (e != cudaSuccess) return fail(FCAS_ERR_CUDA, "fcas_search: %s", cudaGetErrorString(e));
+    return FCAS_OK;
+}
+
+int fcas_gradient(fcas_ctx* c, int64_t n, const double* theta, const int64_t* tc, double* grad, void* stream) {
+    g_last_error.clear();
+    if (!c) return fail(FCAS_ERR_INVALID, "fcas_gradient: NULL context");
+    if (n < 0) return fail(FCAS_ERR_INVALID, "fcas_gradient: n < 0");
+    if (n == 0) return FCAS_OK;
+    if (!theta || !tc || !grad) return fail(FCAS_ERR_INVALID, "fcas_gradient: NULL array");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool th_dev = is_device_ptr(theta), tc_dev = is_device_ptr(tc), g_dev = is_device_ptr(grad);
+    int rc = ensure_particles(c, n);
+    if (rc) return rc;
+    if (!th_dev || !tc_dev) {
+        rc = ensure_staging(c, n);
+        if (rc) return rc;
+    }
+    if (n > c->grad_cap) {
+        if (c->d_gsums) cudaFree(c->d_gsums);
+        if (c->d_gstage) cudaFree(c->d_gstage);
+        c->d_gsums = nullptr;
+        c->d_gstage = nullptr;
+        c->grad_cap = 0;
+        rc = dev_alloc(&c->d_gsums, sizeof(double) * 12 * (size_t)c->setup.n_det * n, "gradient sums");
+        if (!rc) rc = dev_alloc(&c->d_gstage, sizeof(double) * 4 * (size_t)n, "gradient staging");
+        if (rc) return rc;
+        c->grad_cap = n;
+    }
+    const double* d_theta = theta;
+    if (!th_dev) {
+        FCAS_CUDA(cudaMemcpyAsync(c->d_theta, theta, sizeof(double) * 4 * (size_t)n, cudaMemcpyHostToDevice, st));
+        d_theta = c->d_theta;
+    }
+    const int64_t* d_tc = tc;
+    if (!tc_dev) {
+        FCAS_CUDA(cudaMemcpyAsync(c->d_tc, tc, sizeof(int64_t) * (size_t)n, cudaMemcpyHostToDevice, st));
+        d_tc = c->d_tc;
+    }
+    double* d_grad = g_dev ? grad : c->d_gstage;
+    FCAS_CUDA(launch_geometry(d_theta, n, c->d_params, c->d_det, c->d_sigma2s, c->setup.n_det, c->setup.f_low, c->df,
+                              st));
+    const FitnessPlan plan = make_plan(c);
+    const int k1b = pass_a_k1b_for(c->log_n2, c->setup.precision);
+    if (c->setup.precision == FCAS_PREC_FP32)
+        FCAS_CUDA(launch_grad_sums<float>(plan, k1b, c->k_lo, c->k_hi, c->d_params, d_tc, n, c->d_gsums, st));
+    else
+        FCAS_CUDA(launch_grad_sums<double>(plan, k1b, c->k_lo, c->k_hi, c->d_params, d_tc, n, c->d_gsums, st));
+    FCAS_CUDA(launch_grad_final(d_theta, d_tc, n, c->d_gsums, c->d_det, c->d_sigma2s, c->setup.n_det, c->setup.f_low,
+                                c->df, d_grad, st));
+    if (!g_dev) {
+        FCAS_CUDA(cudaMemcpyAsync(grad, d_grad, sizeof(double) * 4 * (size_t)n, cudaMemcpyDeviceToHost, st));
+    }
+    if (!th_dev || !tc_dev || !g_dev) FCAS_CUDA(cudaStreamSynchronize(st));
     return FCAS_OK;
 }
 

@@ -56,6 +56,10 @@ struct fcas_ctx {
     fcas::Partial* d_partials = nullptr;  // [chunk][blocks per particle]
     int64_t chunk = 0;
     int64_t nb_partials = 0;
+    // adjoint
+    double* d_gsums = nullptr;       // [n][D][12] per-detector sums at t*
+    double* d_gstage = nullptr;      // [n][4] gradient staging for host outputs
+    int64_t grad_cap = 0;
     // particle swarm search
     unsigned char* d_pso = nullptr;  // state, parameters, fitness, counters and results of the swarm
     size_t pso_bytes = 0;

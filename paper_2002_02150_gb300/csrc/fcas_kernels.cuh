@@ -58,6 +58,14 @@ int pass_b_blocks_per_particle(int log_n1, int log_n2, int precision);
 int pass_a_k1b_for(int log_n2, int precision);
 cudaError_t launch_stage_tables(int log_l, double2* t64, float2* t32, cudaStream_t s);
 
+// ---- adjoint (fcas_grad.cu) ----
+template <typename Real>
+cudaError_t launch_grad_sums(const FitnessPlan& pl, int k1b, int64_t k_lo, int64_t k_hi, const ParticleParams* params,
+                             const int64_t* tc, int64_t n, double* sums, cudaStream_t s);
+cudaError_t launch_grad_final(const double* theta, const int64_t* tc, int64_t n, const double* sums,
+                              const double* det9, const double* s2, int n_det, double f_star, double df, double* grad,
+                              cudaStream_t s);
+
 // ---- create path (fcas_create.cu) ----
 cudaError_t launch_tables(int log_n, int log_n1, int log_n2, double2* tw64, double2* twlo64, double2* twhi64,
                           float2* tw32, float2* twlo32, float2* twhi32, cudaStream_t s);

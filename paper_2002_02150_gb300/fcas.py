@@ -100,6 +100,8 @@ def load_library():
     lib.fcas_pso_update.restype = i32
     lib.fcas_search.argtypes = [vp, ctypes.POINTER(fcas_pso_config), ctypes.POINTER(fcas_search_result), vp]
     lib.fcas_search.restype = i32
+    lib.fcas_gradient.argtypes = [vp, i64, vp, vp, vp, vp]
+    lib.fcas_gradient.restype = i32
     _lib = lib
     return lib
 
@@ -277,3 +279,90 @@ def fcas_search(ctx, cfg, stream=None):
     s = ctypes.c_void_p(int(stream)) if stream is not None else ctypes.c_void_p(0)
     _check(load_library().fcas_search(ctx.handle, ctypes.byref(cfg), res, s))
     return [dict(fitness=r.fitness, theta=list(r.theta), tc=r.tc, evaluations=r.evaluations) for r in res]
+
+
+def fcas_gradient(ctx, theta, tc, grad=None, stream=None):
+    """d Gamma^2 / d theta at fixed tc (n, 4); output follows theta's memory kind unless given."""
+    n = int(theta.shape[0])
+    if grad is None:
+        if _is_torch(theta) and theta.is_cuda:
+            import torch
+            grad = torch.empty((n, 4), dtype=torch.float64, device=theta.device)
+        else:
+            grad = np.empty((n, 4), dtype=np.float64)
+    p_th, k1 = _ptr(theta, np.float64)
+    p_tc, k2 = _ptr(tc, np.int64)
+    p_g, k3 = _ptr(grad, np.float64)
+    _check(load_library().fcas_gradient(ctx.handle, n, p_th, p_tc, p_g, _stream(stream, theta, tc, grad)))
+    if k3 is not grad and _is_torch(grad):
+        grad.copy_(k3)
+    return k3 if not _is_torch(grad) else grad
+
+
+def _autograd_function():
+    import torch
+
+    class CoherentFitness(torch.autograd.Function):
+        """Gamma^2(theta) with its adjoint: forward = fcas_fitness, backward = fcas_gradient at the
+        forward pass's argmax t_c (the maximisation over t_c is held fixed)."""
+
+        @staticmethod
+        def forward(actx, theta, fctx):
+            fit, tc = fcas_fitness(fctx, theta.detach().contiguous())
+            actx.save_for_backward(theta, tc)
+            actx.fctx = fctx
+            actx.mark_non_differentiable(tc)
+            return fit, tc
+
+        @staticmethod
+        def backward(actx, g_fit, g_tc):
+            theta, tc = actx.saved_tensors
+            grad = fcas_gradient(actx.fctx, theta.detach().contiguous(), tc)
+            return grad * g_fit.unsqueeze(1), None
+
+    return CoherentFitness
+
+
+_CF = None
+
+
+def coherent_fitness(ctx, theta):
+    """Differentiable fitness for torch CUDA tensors: returns (fitness, tc); fitness.backward()
+    propagates d Gamma^2 / d theta through the library's adjoint kernel."""
+    global _CF
+    if _CF is None:
+        _CF = _autograd_function()
+    return _CF.apply(theta, ctx)
+
+
+def polish(ctx, theta, steps=10, scales=(1e-2, 1e-2, 1e-4, 1e-4), judge=None, max_halvings=30):
+    """Gradient ascent from theta (n, 4) numpy: each step moves by s^2 g / |s g| (s = scales, relative
+    for the chirp times) and halves the step until the judge's fitness increases (default judge: this
+    library's fitness). Returns (theta, fitness, accepted steps) per particle."""
+    theta = np.array(theta, dtype=np.float64)
+    if judge is None:
+        judge = lambda th: fcas_fitness(ctx, th)
+    fit, tc = judge(theta)
+    fit = np.array(fit, dtype=np.float64)
+    tc = np.array(tc, dtype=np.int64)
+    accepted = np.zeros(len(theta), dtype=np.int64)
+    for _ in range(steps):
+        g = fcas_gradient(ctx, theta, tc)
+        sc = np.array(scales)[None, :] * np.concatenate([np.ones((len(theta), 2)), theta[:, 2:4]], axis=1)
+        direction = sc * sc * g / np.maximum(np.linalg.norm(sc * g, axis=1, keepdims=True), 1e-300)
+        step = np.ones(len(theta))
+        done = ~np.all(np.isfinite(g), axis=1)
+        for _h in range(max_halvings):
+            if np.all(done):
+                break
+            cand = theta + step[:, None] * direction
+            f2, t2 = judge(cand)
+            f2 = np.array(f2)
+            ok = (~done) & (f2 > fit)
+            theta[ok] = cand[ok]
+            fit[ok] = f2[ok]
+            tc[ok] = np.array(t2)[ok]
+            accepted[ok] += 1
+            done |= ok
+            step[~done] *= 0.5
+    return theta, fit, accepted
