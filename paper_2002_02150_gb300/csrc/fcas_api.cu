@@ -220,7 +220,7 @@ int fcas_create(fcas_ctx** out, const fcas_setup* setup, const fcas_detector* de
     fcas_ctx* c = new fcas_ctx();
     c->setup = s;
     c->log_n = log_n;
-    c->log_n2 = log_n / 2;
+    c->log_n2 = split_log_n2(log_n);
     c->log_n1 = log_n - c->log_n2;
     c->n1 = (int64_t)1 << c->log_n1;
     c->n2 = (int64_t)1 << c->log_n2;

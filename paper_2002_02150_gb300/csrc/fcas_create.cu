@@ -112,14 +112,15 @@ cudaError_t launch_sigma2(const double* psd, int n_det, int64_t row, int64_t k_l
 // n = n1 + N1 n2, k = ka + N2 kb. Pass 1 transforms columns n1 over n2 and applies
 // e^{-2 pi i n1 ka / N}; pass 2 transforms rows ka over n1 into natural order.
 // ------------------------------------------------------------------------------------------
-constexpr int kCreateV = 4;
+__host__ __device__ constexpr int create_v(int log_l) { return log_l >= 13 ? 8 : 4; }
 
 template <int LOG_L>
-__global__ void __launch_bounds__((1 << LOG_L) / kCreateV)
+__global__ void __launch_bounds__((1 << LOG_L) / create_v(LOG_L))
 data_fft_pass1(const double* __restrict__ data, int64_t n_samples, int log_n1, const double2* __restrict__ tw,
                int tw_shift, const double2* __restrict__ twlo, const double2* __restrict__ twhi,
                double2* __restrict__ work) {
     constexpr int L = 1 << LOG_L;
+    constexpr int kCreateV = create_v(LOG_L);
     constexpr int G = L / kCreateV;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double2* smem = reinterpret_cast<double2*>(smem_raw);
@@ -146,10 +147,11 @@ data_fft_pass1(const double* __restrict__ data, int64_t n_samples, int log_n1, c
 }
 
 template <int LOG_L>
-__global__ void __launch_bounds__((1 << LOG_L) / kCreateV)
+__global__ void __launch_bounds__((1 << LOG_L) / create_v(LOG_L))
 data_fft_pass2(const double2* __restrict__ work, int log_n2, const double2* __restrict__ tw, int tw_shift,
                double2* __restrict__ spec) {
     constexpr int L = 1 << LOG_L;
+    constexpr int kCreateV = create_v(LOG_L);
     constexpr int G = L / kCreateV;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double2* smem = reinterpret_cast<double2*>(smem_raw);
@@ -176,7 +178,7 @@ static cudaError_t data_fft_at(const double* data, int n_det, int64_t n_samples,
     auto k = data_fft_pass1<LG>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k<<<dim3((unsigned)(1 << log_n1), (unsigned)n_det), (1 << LG) / kCreateV, smem, s>>>(
+    k<<<dim3((unsigned)(1 << log_n1), (unsigned)n_det), (1 << LG) / create_v(LG), smem, s>>>(
         data, n_samples, log_n1, tw, tw_shift_a, twlo, twhi, work);
     (void)log_n2;
     return cudaGetLastError();
@@ -189,7 +191,7 @@ static cudaError_t data_fft2_at(int n_det, int log_n2, const double2* tw, int tw
     auto k = data_fft_pass2<LG>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k<<<dim3((unsigned)(1 << log_n2), (unsigned)n_det), (1 << LG) / kCreateV, smem, s>>>(work, log_n2, tw, tw_shift_b,
+    k<<<dim3((unsigned)(1 << log_n2), (unsigned)n_det), (1 << LG) / create_v(LG), smem, s>>>(work, log_n2, tw, tw_shift_b,
                                                                                          spec);
     return cudaGetLastError();
 }
@@ -202,7 +204,7 @@ cudaError_t launch_data_fft(const double* data, int n_det, int64_t n_samples, in
     switch (log_n2) {
 #define FCAS_CASE(LG) case LG: e = data_fft_at<LG>(data, n_det, n_samples, log_n1, log_n2, tw64, tw_shift_a, twlo64, twhi64, work, s); break;
         FCAS_CASE(2) FCAS_CASE(3) FCAS_CASE(4) FCAS_CASE(5) FCAS_CASE(6) FCAS_CASE(7) FCAS_CASE(8)
-        FCAS_CASE(9) FCAS_CASE(10) FCAS_CASE(11) FCAS_CASE(12)
+        FCAS_CASE(9) FCAS_CASE(10) FCAS_CASE(11) FCAS_CASE(12) FCAS_CASE(13)
 #undef FCAS_CASE
         default: return cudaErrorInvalidValue;
     }
@@ -210,7 +212,7 @@ cudaError_t launch_data_fft(const double* data, int n_det, int64_t n_samples, in
     switch (log_n1) {
 #define FCAS_CASE(LG) case LG: return data_fft2_at<LG>(n_det, log_n2, tw64, tw_shift_b, work, spec, s);
         FCAS_CASE(2) FCAS_CASE(3) FCAS_CASE(4) FCAS_CASE(5) FCAS_CASE(6) FCAS_CASE(7) FCAS_CASE(8)
-        FCAS_CASE(9) FCAS_CASE(10) FCAS_CASE(11) FCAS_CASE(12)
+        FCAS_CASE(9) FCAS_CASE(10) FCAS_CASE(11) FCAS_CASE(12) FCAS_CASE(13)
 #undef FCAS_CASE
         default: return cudaErrorInvalidValue;
     }

@@ -78,6 +78,9 @@ __host__ __device__ constexpr int imax_c(int a, int b) { return a > b ? a : b; }
 #ifndef FCAS_PASS_A_SUB
 #define FCAS_PASS_A_SUB 8             // adjacent column blocks of one particle scheduled together
 #endif
+#ifndef FCAS_SPLIT_BIAS
+#define FCAS_SPLIT_BIAS 0             // N2 = 2^(floor(log2 N / 2) - bias): a smaller pass-A transform
+#endif
 #ifndef FCAS_PASS_B_THREADS_F32
 #define FCAS_PASS_B_THREADS_F32 256   // target CTA size of pass B, FP32 form
 #endif
@@ -101,8 +104,12 @@ __host__ __device__ constexpr int pass_b_threads(int log_l, int real_bytes) {
 // Transforms per particle between the passes: the two network-weighted series.
 constexpr int kSeries = 2;
 
-// Smallest/largest supported transform lengths.
+// Smallest/largest supported transform lengths; each pass transforms at most 2^13 points.
 constexpr int kMinLogN = 4;
 constexpr int kMaxLogN = 24;
+constexpr int kMaxLogPass = 13;
+__host__ __device__ constexpr int split_log_n2(int log_n) {
+    return imax_c(2, imax_c(log_n - kMaxLogPass, log_n / 2 - FCAS_SPLIT_BIAS));
+}
 
 }  // namespace fcas

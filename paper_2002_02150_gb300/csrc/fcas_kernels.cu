@@ -326,7 +326,7 @@ __device__ __forceinline__ bool better_f(float v, int t, float bv, int bt) {
 }
 
 template <typename Real, int LOG_L>
-__global__ void __launch_bounds__(pass_b_threads(LOG_L, sizeof(Real)), 2)
+__global__ void __launch_bounds__(pass_b_threads(LOG_L, sizeof(Real)), pass_b_threads(LOG_L, sizeof(Real)) <= 256 ? 2 : 1)
 pass_b_kernel(const cplx<Real>* __restrict__ inter, const ParticleParams* __restrict__ params, int64_t p0,
               int log_n2, int64_t n_samples, const cplx<Real>* __restrict__ stw, Partial* __restrict__ partials) {
     using C = cplx<Real>;
@@ -446,7 +446,7 @@ cudaError_t launch_reduce(const Partial* partials, int64_t nb, const ParticlePar
 // ------------------------------------------------------------------------------------------
 // dispatch on the transform lengths
 // ------------------------------------------------------------------------------------------
-#define FCAS_LOG_CASES(X) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12)
+#define FCAS_LOG_CASES(X) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13)
 
 int pass_a_k1b_for(int log_n2, int precision) {
     const int rb = precision == FCAS_PREC_FP32 ? 4 : 8;
