@@ -67,8 +67,12 @@ typedef struct fcas_setup {
     double f_low;        /* lower cutoff f_* [Hz] (> 0): the template is zero for f <= f_low (Sec. II.B) */
     double f_high;       /* upper cutoff [Hz]: the template is zero for f > f_high (Sec. II.B) */
     int32_t max_batch;   /* particles per internal chunk (0 = automatic); bounds scratch memory */
-    int32_t reserved;    /* must be 0 */
+    int32_t flags;       /* 0 or FCAS_SETUP_LAZY_SCRATCH */
 } fcas_setup;
+
+/* fcas_setup.flags: do not allocate the fitness scratch at create (a context that only takes part
+ * in a group uses the group's shared scratch; fcas_fitness allocates it on first use). */
+#define FCAS_SETUP_LAZY_SCRATCH 1
 
 typedef struct fcas_ctx fcas_ctx;
 
@@ -212,6 +216,46 @@ int fcas_search(fcas_ctx* ctx, const fcas_pso_config* cfg, fcas_search_result* r
  */
 int fcas_gradient(fcas_ctx* ctx, int64_t n, const double* theta, const int64_t* tc, double* grad, void* stream);
 
+/*
+ * fcas_autotune -- choose the launch shapes of the fitness path for this context by timing them:
+ * the N = n1 n2 split (balanced, or a pass-A transform half as long), the number of columns per
+ * pass-A CTA among the compiled widths, and how many adjacent column blocks of a particle are
+ * scheduled together (1, 4, 8, 16). Each candidate evaluates n_particles particles (one warm-up,
+ * three timed launches, CUDA events); the fastest is kept (the spectrum is laid out again for it).
+ * cache_path (may be NULL): a text file of earlier results keyed by GPU name, n_fft, n_det,
+ * precision and n_particles; a hit is applied without timing, a miss is timed and appended.
+ * Synchronous.
+ */
+int fcas_autotune(fcas_ctx* ctx, int64_t n_particles, const char* cache_path, void* stream);
+
+/*
+ * Groups: several prepared segments (e.g. noise realisations of different durations, so different
+ * n_fft) searched together. The contexts share one scratch pool sized for the largest; every PSO
+ * iteration of every segment's swarm is one CUDA-graph launch that runs all segments' parameter,
+ * fitness and update kernels back to back. The contexts stay owned by the caller and must outlive
+ * the group; create them with FCAS_SETUP_LAZY_SCRATCH to avoid per-context scratch.
+ */
+typedef struct fcas_group fcas_group;
+
+/*
+ * fcas_set_shape -- pin the launch shape without timing: split_bias 0 or 1, k1b one of the compiled
+ * pass-A widths for the resulting length (0 = default), sub a power of two. FCAS_ERR_INVALID for a
+ * shape that is not available. Synchronous.
+ */
+int fcas_set_shape(fcas_ctx* ctx, int32_t split_bias, int32_t k1b, int32_t sub, void* stream);
+
+/* max_batch: particles per chunk of the shared scratch (0 = automatic, <= 64). */
+int fcas_group_create(fcas_group** out, int32_t n_ctx, fcas_ctx* const* ctxs, int32_t max_batch);
+
+/*
+ * fcas_group_search -- one swarm of cfg per segment (segment s draws its random numbers with the
+ * key seed + s * 0x9E3779B97F4A7C15), all advanced together for cfg->n_iter iterations.
+ * results: host array [n_ctx][n_runs]. Synchronous.
+ */
+int fcas_group_search(fcas_group* group, const fcas_pso_config* cfg, fcas_search_result* results, void* stream);
+
+void fcas_group_destroy(fcas_group* group);
+
 /* Release every resource held by the context (NULL is a no-op). Synchronises the device. */
 void fcas_destroy(fcas_ctx* ctx);
 
@@ -232,6 +276,11 @@ typedef struct fcas_info {
     double sigma2[FCAS_MAX_DET];/* unscaled template norms <h_c|h_c>^i */
     int64_t inter_bytes;        /* bytes per particle that cross HBM between the two FFT passes */
     int64_t series;             /* length-N transforms per particle (2: the network-weighted series) */
+    int32_t split_bias;         /* n2 = 2^(floor(log2 n_fft / 2) - split_bias) */
+    int32_t k1b;                /* pass-A columns per CTA */
+    int32_t sub;                /* pass-A column blocks of a particle scheduled together */
+    int32_t pad;
+    double tuned_ms_per_particle; /* time per particle of the tuned shape (0: not tuned) */
 } fcas_info;
 
 int fcas_get_info(const fcas_ctx* ctx, fcas_info* info);

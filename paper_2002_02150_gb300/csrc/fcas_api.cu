@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -59,7 +60,7 @@ void free_ctx(fcas_ctx* c) {
     void* ptrs[] = {c->d_det, c->d_sigma2s, c->d_y, c->d_basis, c->d_tw64, c->d_twlo64, c->d_twhi64,
                     c->d_tw32, c->d_twlo32, c->d_twhi32, c->d_stw_a64, c->d_stw_a32, c->d_stw_b64, c->d_stw_b32,
                     c->d_params, c->d_theta, c->d_fit, c->d_tc, c->d_inter, c->d_partials, c->d_pso,
-                    c->d_gsums, c->d_gstage};
+                    c->d_gsums, c->d_gstage, c->d_ynat};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->search_stream) cudaStreamDestroy(c->search_stream);
@@ -138,29 +139,77 @@ void prof_end(fcas_ctx* c, size_t slot, cudaStream_t s) {
     if (slot != SIZE_MAX) cudaEventRecord(c->events[slot].b, s);
 }
 
-// Passes A, B and the final argmax over chunks of the context's particle parameters.
-cudaError_t launch_passes(fcas_ctx* c, int64_t n, double* d_fit, int64_t* d_tc, cudaStream_t st) {
+// Passes A, B and the final argmax over chunks of particle parameters, with the given scratch.
+cudaError_t launch_passes_with(fcas_ctx* c, const ParticleParams* params, void* inter, Partial* partials,
+                               int64_t chunk, int64_t n, double* d_fit, int64_t* d_tc, cudaStream_t st) {
     const FitnessPlan plan = make_plan(c);
     const bool fp32 = c->setup.precision == FCAS_PREC_FP32;
     size_t slot;
     cudaError_t e = cudaSuccess;
-    for (int64_t p0 = 0; p0 < n && e == cudaSuccess; p0 += c->chunk) {
-        const int64_t np = (n - p0) < c->chunk ? (n - p0) : c->chunk;
+    for (int64_t p0 = 0; p0 < n && e == cudaSuccess; p0 += chunk) {
+        const int64_t np = (n - p0) < chunk ? (n - p0) : chunk;
         prof_begin(c, FCAS_KERNEL_PASS_A, st, &slot);
-        e = fp32 ? launch_pass_a<float>(plan, c->d_params, p0, np, c->d_inter, st)
-                 : launch_pass_a<double>(plan, c->d_params, p0, np, c->d_inter, st);
+        e = fp32 ? launch_pass_a<float>(plan, params, p0, np, inter, st)
+                 : launch_pass_a<double>(plan, params, p0, np, inter, st);
         prof_end(c, slot, st);
         if (e != cudaSuccess) break;
         prof_begin(c, FCAS_KERNEL_PASS_B, st, &slot);
-        e = fp32 ? launch_pass_b<float>(plan, c->d_params, p0, np, c->d_inter, c->d_partials, st)
-                 : launch_pass_b<double>(plan, c->d_params, p0, np, c->d_inter, c->d_partials, st);
+        e = fp32 ? launch_pass_b<float>(plan, params, p0, np, inter, partials, st)
+                 : launch_pass_b<double>(plan, params, p0, np, inter, partials, st);
         prof_end(c, slot, st);
         if (e != cudaSuccess) break;
         prof_begin(c, FCAS_KERNEL_REDUCE, st, &slot);
-        e = launch_reduce(c->d_partials, c->nb_partials, c->d_params, p0, np, d_fit, d_tc, st);
+        e = launch_reduce(partials, c->nb_partials, params, p0, np, d_fit, d_tc, st);
         prof_end(c, slot, st);
     }
     return e;
+}
+
+cudaError_t launch_passes(fcas_ctx* c, int64_t n, double* d_fit, int64_t* d_tc, cudaStream_t st) {
+    return launch_passes_with(c, c->d_params, c->d_inter, c->d_partials, c->chunk, n, d_fit, d_tc, st);
+}
+
+// Scratch of the fitness path (allocated at create unless FCAS_SETUP_LAZY_SCRATCH, else on first use).
+int ensure_scratch(fcas_ctx* c) {
+    if (c->d_inter) return FCAS_OK;
+    const size_t per_particle = inter_bytes_per_particle(c->setup.precision, c->setup.n_fft);
+    int rc = dev_alloc(&c->d_inter, per_particle * (size_t)c->chunk, "intermediate transform");
+    if (!rc) rc = dev_alloc(&c->d_partials, sizeof(Partial) * (size_t)c->chunk * c->nb_cap, "argmax partials");
+    return rc;
+}
+
+// Choose the N = N1 N2 split (bias), the pass-A column-block width (k1b; 0 = the default) and the
+// CTA grouping (sub), and lay the spectrum out for them.
+int apply_layout(fcas_ctx* c, int bias, int k1b, int sub, cudaStream_t st) {
+    const int log_n = c->log_n;
+    const int l2 = split_log_n2_with(log_n, bias);
+    const int l1 = log_n - l2;
+    if (l1 > kMaxLogPass) return fail(FCAS_ERR_INVALID, "split bias %d gives a %d-point pass", bias, 1 << l1);
+    int ks[3];
+    const int nk = pass_a_k1b_variants(l2, c->setup.precision, ks);
+    if (nk <= 0) return fail(FCAS_ERR_INVALID, "no pass-A shape for 2^%d-point columns", l2);
+    if (k1b == 0) k1b = ks[0];
+    bool ok = false;
+    for (int q = 0; q < nk; ++q) ok |= ks[q] == k1b;
+    if (!ok) return fail(FCAS_ERR_INVALID, "pass-A width %d not compiled for 2^%d-point columns", k1b, l2);
+    if (sub < 1 || (sub & (sub - 1))) return fail(FCAS_ERR_INVALID, "CTA grouping %d is not a power of two", sub);
+    const int64_t nb = pass_b_blocks_per_particle(l1, l2, c->setup.precision);
+    if (c->nb_cap && nb > c->nb_cap) return fail(FCAS_ERR_INVALID, "split bias %d needs more argmax partials", bias);
+    c->split_bias = bias;
+    c->log_n2 = l2;
+    c->log_n1 = l1;
+    c->n1 = (int64_t)1 << l1;
+    c->n2 = (int64_t)1 << l2;
+    c->k1b = k1b;
+    c->sub = sub;
+    c->nb_partials = nb;
+    cudaError_t e = launch_stage_tables(l2, c->d_stw_a64, c->d_stw_a32, st);
+    if (e == cudaSuccess) e = launch_stage_tables(l1, c->d_stw_b64, c->d_stw_b32, st);
+    if (e == cudaSuccess)
+        e = launch_layout(c->d_ynat, c->setup.n_det, log_n, l1, l2, k1b, c->k_lo, c->k_hi, c->setup.fs, c->setup.f_low,
+                          c->setup.precision, c->d_y, c->d_basis, st);
+    if (e != cudaSuccess) return fail(FCAS_ERR_CUDA, "layout: %s", cudaGetErrorString(e));
+    return FCAS_OK;
 }
 
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
@@ -192,7 +241,8 @@ int fcas_create(fcas_ctx** out, const fcas_setup* setup, const fcas_detector* de
     if (!(std::isfinite(s.fs) && s.fs > 0.0)) return fail(FCAS_ERR_INVALID, "fs must be finite and > 0");
     if (!(std::isfinite(s.f_low) && std::isfinite(s.f_high) && s.f_low > 0.0 && s.f_high > s.f_low))
         return fail(FCAS_ERR_INVALID, "need 0 < f_low < f_high (finite)");
-    if (s.max_batch < 0 || s.reserved != 0) return fail(FCAS_ERR_INVALID, "max_batch < 0 or reserved != 0");
+    if (s.max_batch < 0 || (s.flags & ~FCAS_SETUP_LAZY_SCRATCH) != 0)
+        return fail(FCAS_ERR_INVALID, "max_batch < 0 or unknown bits in flags");
     for (int i = 0; i < s.n_det; ++i) {
         const double* v = det[i].r;
         for (int q = 0; q < 9; ++q)
@@ -220,7 +270,7 @@ int fcas_create(fcas_ctx** out, const fcas_setup* setup, const fcas_detector* de
     fcas_ctx* c = new fcas_ctx();
     c->setup = s;
     c->log_n = log_n;
-    c->log_n2 = split_log_n2(log_n);
+    c->log_n2 = split_log_n2_with(log_n, FCAS_SPLIT_BIAS);
     c->log_n1 = log_n - c->log_n2;
     c->n1 = (int64_t)1 << c->log_n1;
     c->n2 = (int64_t)1 << c->log_n2;
@@ -315,12 +365,6 @@ int fcas_create(fcas_ctx** out, const fcas_setup* setup, const fcas_detector* de
     FCAS_TRY(dev_alloc(&c->d_twhi32, sizeof(float2) * nhi, "twiddles"));
     FCAS_TRYCUDA(launch_tables(log_n, c->log_n1, c->log_n2, c->d_tw64, c->d_twlo64, c->d_twhi64, c->d_tw32,
                                c->d_twlo32, c->d_twhi32, st));
-    FCAS_TRY(dev_alloc(&c->d_stw_a64, sizeof(double2) * ((size_t)1 << c->log_n2), "stage twiddles"));
-    FCAS_TRY(dev_alloc(&c->d_stw_a32, sizeof(float2) * ((size_t)1 << c->log_n2), "stage twiddles"));
-    FCAS_TRY(dev_alloc(&c->d_stw_b64, sizeof(double2) * ((size_t)1 << c->log_n1), "stage twiddles"));
-    FCAS_TRY(dev_alloc(&c->d_stw_b32, sizeof(float2) * ((size_t)1 << c->log_n1), "stage twiddles"));
-    FCAS_TRYCUDA(launch_stage_tables(c->log_n2, c->d_stw_a64, c->d_stw_a32, st));
-    FCAS_TRYCUDA(launch_stage_tables(c->log_n1, c->d_stw_b64, c->d_stw_b32, st));
     const bool fp32 = s.precision == FCAS_PREC_FP32;
     c->d_tw = fp32 ? (void*)c->d_tw32 : (void*)c->d_tw64;
     c->d_twlo = fp32 ? (void*)c->d_twlo32 : (void*)c->d_twlo64;
@@ -332,14 +376,19 @@ int fcas_create(fcas_ctx** out, const fcas_setup* setup, const fcas_detector* de
     FCAS_TRYCUDA(launch_data_fft(d_data, D, s.n_samples, log_n, c->log_n1, c->log_n2, c->d_tw64, log_tw - c->log_n2,
                                  log_tw - c->log_n1, c->d_twlo64, c->d_twhi64, d_work, d_spec, st));
     const size_t half = (size_t)(n / 2);
+    FCAS_TRY(dev_alloc(&c->d_ynat, sizeof(double2) * (size_t)D * half, "whitened spectrum (natural order)"));
+    FCAS_TRYCUDA(launch_whiten(d_spec, d_psd, D, psd_row, log_n, k_lo, k_hi, s.fs, c->scale, c->d_ynat, st));
     const size_t ysz = (fp32 ? sizeof(float2) : sizeof(double2)) * (size_t)D * half;
     const size_t bsz = (fp32 ? sizeof(BasisF) : sizeof(BasisD)) * half;
     FCAS_TRY(dev_alloc(&c->d_y, ysz, "whitened spectrum"));
     FCAS_TRY(dev_alloc(&c->d_basis, bsz, "chirp basis"));
-    FCAS_TRYCUDA(launch_prep(d_spec, d_psd, D, psd_row, log_n, c->log_n1, c->log_n2, k_lo, k_hi, s.fs, s.f_low,
-                             c->scale, s.precision, c->d_y, c->d_basis, st));
+    FCAS_TRY(dev_alloc(&c->d_stw_a64, sizeof(double2) << kMaxLogPass, "stage twiddles"));
+    FCAS_TRY(dev_alloc(&c->d_stw_a32, sizeof(float2) << kMaxLogPass, "stage twiddles"));
+    FCAS_TRY(dev_alloc(&c->d_stw_b64, sizeof(double2) << kMaxLogPass, "stage twiddles"));
+    FCAS_TRY(dev_alloc(&c->d_stw_b32, sizeof(float2) << kMaxLogPass, "stage twiddles"));
+    FCAS_TRY(apply_layout(c, FCAS_SPLIT_BIAS, 0, FCAS_PASS_A_SUB, st));
 
-    // scratch for the fitness path
+    // scratch for the fitness path (partials sized for every split the tuner may choose)
     const size_t per_particle = inter_bytes_per_particle(s.precision, n);
     int64_t chunk = s.max_batch;
     if (chunk == 0) {
@@ -349,9 +398,13 @@ int fcas_create(fcas_ctx** out, const fcas_setup* setup, const fcas_detector* de
         if (chunk < 1) chunk = 1;
     }
     c->chunk = chunk;
-    c->nb_partials = pass_b_blocks_per_particle(c->log_n1, c->log_n2, s.precision);
-    FCAS_TRY(dev_alloc(&c->d_inter, per_particle * (size_t)chunk, "intermediate transform"));
-    FCAS_TRY(dev_alloc(&c->d_partials, sizeof(Partial) * (size_t)chunk * c->nb_partials, "argmax partials"));
+    c->nb_cap = 0;
+    for (int bias = 0; bias <= 1; ++bias) {
+        const int l2 = split_log_n2_with(log_n, bias);
+        const int64_t nb = pass_b_blocks_per_particle(log_n - l2, l2, s.precision);
+        if (nb > c->nb_cap) c->nb_cap = nb;
+    }
+    if (!(s.flags & FCAS_SETUP_LAZY_SCRATCH)) FCAS_TRY(ensure_scratch(c));
     FCAS_TRYCUDA(cudaStreamSynchronize(st));
 #undef FCAS_TRY
 #undef FCAS_TRYCUDA
@@ -378,6 +431,7 @@ int fcas_fitness(fcas_ctx* c, int64_t n, const double* theta, double* fitness, i
         }
     }
     int rc = ensure_particles(c, n);
+    if (!rc) rc = ensure_scratch(c);
     if (rc) return rc;
     if (!th_dev || !f_dev || !t_dev) {
         rc = ensure_staging(c, n);
@@ -402,6 +456,86 @@ int fcas_fitness(fcas_ctx* c, int64_t n, const double* theta, double* fitness, i
     return FCAS_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Device buffers of one swarm: state, parameters, fitness, counters and results.
+struct Swarm {
+    PsoStateDev s;
+    double* theta;
+    double* fit;
+    int64_t* tcs;
+    fcas_search_result* res;
+};
+
+size_t swarm_bytes(int64_t rows, int runs) {
+    const size_t r4 = align256(sizeof(double) * 4 * rows), r1 = align256(sizeof(double) * rows);
+    const size_t ri = align256(sizeof(int64_t) * rows);
+    return 4 * r4 + 2 * r1 + 2 * ri + align256(sizeof(int32_t) * runs) + align256(sizeof(int64_t) * runs) +
+           align256(sizeof(fcas_search_result) * runs);
+}
+
+Swarm carve_swarm(unsigned char* b, int64_t rows, int runs) {
+    const size_t r4 = align256(sizeof(double) * 4 * rows), r1 = align256(sizeof(double) * rows);
+    const size_t ri = align256(sizeof(int64_t) * rows);
+    Swarm w;
+    w.s.x = reinterpret_cast<double*>(b);
+    w.s.v = reinterpret_cast<double*>(b + r4);
+    w.s.pbest_x = reinterpret_cast<double*>(b + 2 * r4);
+    w.theta = reinterpret_cast<double*>(b + 3 * r4);
+    w.s.pbest_f = reinterpret_cast<double*>(b + 4 * r4);
+    w.fit = reinterpret_cast<double*>(b + 4 * r4 + r1);
+    w.s.pbest_tc = reinterpret_cast<int64_t*>(b + 4 * r4 + 2 * r1);
+    w.tcs = reinterpret_cast<int64_t*>(b + 4 * r4 + 2 * r1 + ri);
+    size_t off = 4 * r4 + 2 * r1 + 2 * ri;
+    w.s.iter = reinterpret_cast<int32_t*>(b + off);
+    off += align256(sizeof(int32_t) * runs);
+    w.s.evals = reinterpret_cast<int64_t*>(b + off);
+    off += align256(sizeof(int64_t) * runs);
+    w.res = reinterpret_cast<fcas_search_result*>(b + off);
+    return w;
+}
+
+// One PSO iteration of one segment: parameters of the particles inside the box, their fitness, update.
+cudaError_t swarm_iteration(fcas_ctx* c, const PsoDev& g, const Swarm& w, ParticleParams* params, void* inter,
+                            Partial* partials, int64_t chunk, int64_t rows, cudaStream_t st) {
+    cudaError_t x = launch_pso_theta(g, w.s, w.theta, st);
+    if (x == cudaSuccess)
+        x = launch_geometry(w.theta, rows, params, c->d_det, c->d_sigma2s, c->setup.n_det, c->setup.f_low, c->df, st);
+    if (x == cudaSuccess) x = launch_passes_with(c, params, inter, partials, chunk, rows, w.fit, w.tcs, st);
+    if (x == cudaSuccess) x = launch_pso_update(g, 0, w.fit, w.tcs, w.s, st);
+    return x;
+}
+
+// Run `iteration` n_iter times on stream st: the first eagerly (it also sets the kernels' shared
+// memory attributes), the others as replays of a captured graph of it.
+template <typename F>
+cudaError_t run_iterations(int n_iter, cudaStream_t st, F&& iteration) {
+    cudaError_t e = iteration();
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    if (e == cudaSuccess && n_iter > 1) {
+        e = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed);
+        if (e == cudaSuccess) {
+            cudaError_t ei = iteration();
+            e = cudaStreamEndCapture(st, &graph);
+            if (e == cudaSuccess) e = ei;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        for (int it = 1; it < n_iter && e == cudaSuccess; ++it) e = cudaGraphLaunch(exec, st);
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    return e;
+}
+
+uint64_t segment_seed(uint64_t seed, int s) { return seed + (uint64_t)s * 0x9E3779B97F4A7C15ull; }
+
+}  // namespace
+
+extern "C" {
+
 int fcas_search(fcas_ctx* c, const fcas_pso_config* cfg, fcas_search_result* results, void* stream) {
     g_last_error.clear();
     if (!c || !results) return fail(FCAS_ERR_INVALID, "fcas_search: NULL argument");
@@ -410,13 +544,9 @@ int fcas_search(fcas_ctx* c, const fcas_pso_config* cfg, fcas_search_result* res
     if (rc) return fail(rc, "fcas_search: %s", msg);
     const int64_t rows = (int64_t)cfg->n_runs * cfg->n_particles;
     rc = ensure_particles(c, rows);
+    if (!rc) rc = ensure_scratch(c);
     if (rc) return rc;
-    // one allocation: x, v, pbest_x, theta [rows][4]; pbest_f, fitness [rows]; pbest_tc, tc [rows];
-    // iteration and evaluation counters [runs]; results [runs]
-    const size_t r4 = align256(sizeof(double) * 4 * rows), r1 = align256(sizeof(double) * rows);
-    const size_t ri = align256(sizeof(int64_t) * rows);
-    const size_t need = 4 * r4 + 2 * r1 + 2 * ri + align256(sizeof(int32_t) * cfg->n_runs) +
-                        align256(sizeof(int64_t) * cfg->n_runs) + align256(sizeof(fcas_search_result) * cfg->n_runs);
+    const size_t need = swarm_bytes(rows, cfg->n_runs);
     if (need > c->pso_bytes) {
         if (c->d_pso) cudaFree(c->d_pso);
         c->d_pso = nullptr;
@@ -425,69 +555,264 @@ int fcas_search(fcas_ctx* c, const fcas_pso_config* cfg, fcas_search_result* res
         if (rc) return rc;
         c->pso_bytes = need;
     }
-    unsigned char* b = c->d_pso;
-    PsoStateDev s;
-    s.x = reinterpret_cast<double*>(b);
-    s.v = reinterpret_cast<double*>(b + r4);
-    s.pbest_x = reinterpret_cast<double*>(b + 2 * r4);
-    double* theta = reinterpret_cast<double*>(b + 3 * r4);
-    s.pbest_f = reinterpret_cast<double*>(b + 4 * r4);
-    double* fit = reinterpret_cast<double*>(b + 4 * r4 + r1);
-    s.pbest_tc = reinterpret_cast<int64_t*>(b + 4 * r4 + 2 * r1);
-    int64_t* tcs = reinterpret_cast<int64_t*>(b + 4 * r4 + 2 * r1 + ri);
-    size_t off = 4 * r4 + 2 * r1 + 2 * ri;
-    s.iter = reinterpret_cast<int32_t*>(b + off);
-    off += align256(sizeof(int32_t) * cfg->n_runs);
-    s.evals = reinterpret_cast<int64_t*>(b + off);
-    off += align256(sizeof(int64_t) * cfg->n_runs);
-    fcas_search_result* d_res = reinterpret_cast<fcas_search_result*>(b + off);
-
+    const Swarm w = carve_swarm(c->d_pso, rows, cfg->n_runs);
     if (!c->search_stream) FCAS_CUDA(cudaStreamCreateWithFlags(&c->search_stream, cudaStreamNonBlocking));
     cudaStream_t st = c->search_stream;
-    cudaStream_t user = static_cast<cudaStream_t>(stream);
     cudaEvent_t ev;
     FCAS_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-    cudaEventRecord(ev, user);
+    cudaEventRecord(ev, static_cast<cudaStream_t>(stream));
     cudaStreamWaitEvent(st, ev, 0);
     const PsoDev g = pso_dev(cfg);
     const bool prof = c->prof;
     c->prof = false;
-    cudaError_t e = launch_pso_init(g, s, st);
-    // one iteration: parameters of the particles inside the box, their fitness, the swarm update
-    auto iteration = [&]() -> cudaError_t {
-        cudaError_t x = launch_pso_theta(g, s, theta, st);
-        if (x == cudaSuccess)
-            x = launch_geometry(theta, rows, c->d_params, c->d_det, c->d_sigma2s, c->setup.n_det, c->setup.f_low,
-                                c->df, st);
-        if (x == cudaSuccess) x = launch_passes(c, rows, fit, tcs, st);
-        if (x == cudaSuccess) x = launch_pso_update(g, 0, fit, tcs, s, st);
-        return x;
-    };
-    // the first iteration runs eagerly (it also sets the kernels' shared-memory attributes);
-    // the others replay a graph of it
-    if (e == cudaSuccess) e = iteration();
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    if (e == cudaSuccess && cfg->n_iter > 1) {
-        e = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed);
-        if (e == cudaSuccess) {
-            cudaError_t ei = iteration();
-            e = cudaStreamEndCapture(st, &graph);
-            if (e == cudaSuccess) e = ei;
-        }
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
-        for (int it = 1; it < cfg->n_iter && e == cudaSuccess; ++it) e = cudaGraphLaunch(exec, st);
-    }
-    if (e == cudaSuccess) e = launch_pso_result(g, s, d_res, st);
+    cudaError_t e = launch_pso_init(g, w.s, st);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(results, d_res, sizeof(fcas_search_result) * cfg->n_runs, cudaMemcpyDeviceToHost, st);
+        e = run_iterations(cfg->n_iter, st,
+                           [&]() { return swarm_iteration(c, g, w, c->d_params, c->d_inter, c->d_partials, c->chunk,
+                                                          rows, st); });
+    if (e == cudaSuccess) e = launch_pso_result(g, w.s, w.res, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(results, w.res, sizeof(fcas_search_result) * cfg->n_runs, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (exec) cudaGraphExecDestroy(exec);
-    if (graph) cudaGraphDestroy(graph);
     cudaEventDestroy(ev);
     c->prof = prof;
     if (e != cudaSuccess) return fail(FCAS_ERR_CUDA, "fcas_search: %s", cudaGetErrorString(e));
     return FCAS_OK;
+}
+
+int fcas_autotune(fcas_ctx* c, int64_t n_particles, const char* cache_path, void* stream) {
+    g_last_error.clear();
+    if (!c) return fail(FCAS_ERR_INVALID, "fcas_autotune: NULL context");
+    if (n_particles < 1) return fail(FCAS_ERR_INVALID, "fcas_autotune: n_particles < 1");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int dev = 0;
+    cudaDeviceProp prop;
+    FCAS_CUDA(cudaGetDevice(&dev));
+    FCAS_CUDA(cudaGetDeviceProperties(&prop, dev));
+    std::string gpu(prop.name);
+    for (char& ch : gpu)
+        if (ch == ' ') ch = '_';
+    char key[512];
+    snprintf(key, sizeof(key), "fcas-tune-v1 %s %lld %d %d %lld", gpu.c_str(), (long long)c->setup.n_fft,
+             c->setup.n_det, c->setup.precision, (long long)n_particles);
+    if (cache_path) {
+        if (FILE* f = fopen(cache_path, "r")) {
+            char line[1024];
+            while (fgets(line, sizeof(line), f)) {
+                if (strncmp(line, key, strlen(key)) != 0 || line[strlen(key)] != ' ') continue;
+                int bias, k1b, sub;
+                double ms;
+                if (sscanf(line + strlen(key), "%d %d %d %lf", &bias, &k1b, &sub, &ms) == 4) {
+                    fclose(f);
+                    int rc = apply_layout(c, bias, k1b, sub, st);
+                    if (rc) return rc;
+                    c->tuned_ms = ms;
+                    FCAS_CUDA(cudaStreamSynchronize(st));
+                    return FCAS_OK;
+                }
+            }
+            fclose(f);
+        }
+    }
+    int rc = ensure_particles(c, n_particles);
+    if (!rc) rc = ensure_scratch(c);
+    if (!rc) rc = ensure_staging(c, n_particles);
+    if (rc) return rc;
+    std::vector<double> th(4 * (size_t)n_particles);
+    for (int64_t p = 0; p < n_particles; ++p) {   // any valid parameters: the cost does not depend on them
+        th[4 * p + 0] = 0.1 * (double)(p % 60);
+        th[4 * p + 1] = -1.2 + 0.04 * (double)(p % 60);
+        th[4 * p + 2] = 1.0 + 0.01 * (double)(p % 50);
+        th[4 * p + 3] = 0.1 + 0.001 * (double)(p % 50);
+    }
+    FCAS_CUDA(cudaMemcpyAsync(c->d_theta, th.data(), sizeof(double) * th.size(), cudaMemcpyHostToDevice, st));
+    FCAS_CUDA(launch_geometry(c->d_theta, n_particles, c->d_params, c->d_det, c->d_sigma2s, c->setup.n_det,
+                              c->setup.f_low, c->df, st));
+    cudaEvent_t e0, e1;
+    FCAS_CUDA(cudaEventCreate(&e0));
+    FCAS_CUDA(cudaEventCreate(&e1));
+    const bool prof = c->prof;
+    c->prof = false;
+    double best_ms = 1e300;
+    int best_bias = c->split_bias, best_k = c->k1b, best_sub = c->sub;
+    int last_l2 = -1;
+    const int subs[4] = {1, 4, 8, 16};
+    for (int bias = 0; bias <= 1 && rc == FCAS_OK; ++bias) {
+        const int l2 = split_log_n2_with(c->log_n, bias);
+        if (l2 == last_l2 || c->log_n - l2 > kMaxLogPass) continue;
+        last_l2 = l2;
+        int ks[3];
+        const int nk = pass_a_k1b_variants(l2, c->setup.precision, ks);
+        for (int q = 0; q < nk && rc == FCAS_OK; ++q) {
+            for (int si = 0; si < 4 && rc == FCAS_OK; ++si) {
+                rc = apply_layout(c, bias, ks[q], subs[si], st);
+                if (rc) break;
+                cudaError_t e = launch_passes(c, n_particles, c->d_fit, c->d_tc, st);   // warm-up
+                if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+                for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch_passes(c, n_particles, c->d_fit, c->d_tc, st);
+                if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (e != cudaSuccess) {
+                    rc = fail(FCAS_ERR_CUDA, "fcas_autotune: %s", cudaGetErrorString(e));
+                    break;
+                }
+                const double per = ms / 3.0 / (double)n_particles;
+                if (per < best_ms) {
+                    best_ms = per;
+                    best_bias = bias;
+                    best_k = ks[q];
+                    best_sub = subs[si];
+                }
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->prof = prof;
+    if (rc) return rc;
+    rc = apply_layout(c, best_bias, best_k, best_sub, st);
+    if (rc) return rc;
+    c->tuned_ms = best_ms;
+    FCAS_CUDA(cudaStreamSynchronize(st));
+    if (cache_path) {
+        if (FILE* f = fopen(cache_path, "a")) {
+            fprintf(f, "%s %d %d %d %.9g\n", key, best_bias, best_k, best_sub, best_ms);
+            fclose(f);
+        }
+    }
+    return FCAS_OK;
+}
+
+int fcas_set_shape(fcas_ctx* c, int32_t split_bias, int32_t k1b, int32_t sub, void* stream) {
+    g_last_error.clear();
+    if (!c) return fail(FCAS_ERR_INVALID, "fcas_set_shape: NULL context");
+    if (split_bias < 0 || split_bias > 1) return fail(FCAS_ERR_INVALID, "fcas_set_shape: split_bias must be 0 or 1");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = apply_layout(c, split_bias, k1b, sub, st);
+    if (rc) return rc;
+    c->tuned_ms = 0.0;
+    FCAS_CUDA(cudaStreamSynchronize(st));
+    return FCAS_OK;
+}
+
+}  // extern "C"
+
+struct fcas_group {
+    std::vector<fcas_ctx*> ctxs;
+    int64_t chunk = 0;
+    void* d_inter = nullptr;
+    Partial* d_partials = nullptr;
+    ParticleParams* d_params = nullptr;
+    int64_t params_cap = 0;
+    unsigned char* d_pso = nullptr;
+    size_t pso_bytes = 0;
+    cudaStream_t st = nullptr;
+};
+
+extern "C" {
+
+int fcas_group_create(fcas_group** out, int32_t n_ctx, fcas_ctx* const* ctxs, int32_t max_batch) {
+    g_last_error.clear();
+    if (!out || !ctxs || n_ctx < 1) return fail(FCAS_ERR_INVALID, "fcas_group_create: need n_ctx >= 1 contexts");
+    if (max_batch < 0) return fail(FCAS_ERR_INVALID, "fcas_group_create: max_batch < 0");
+    *out = nullptr;
+    size_t inter_pp = 0;
+    int64_t nb = 0;
+    for (int i = 0; i < n_ctx; ++i) {
+        if (!ctxs[i]) return fail(FCAS_ERR_INVALID, "fcas_group_create: context %d is NULL", i);
+        const size_t b = inter_bytes_per_particle(ctxs[i]->setup.precision, ctxs[i]->setup.n_fft);
+        if (b > inter_pp) inter_pp = b;
+        if (ctxs[i]->nb_cap > nb) nb = ctxs[i]->nb_cap;
+    }
+    fcas_group* g = new fcas_group();
+    g->ctxs.assign(ctxs, ctxs + n_ctx);
+    int64_t chunk = max_batch;
+    if (chunk == 0) chunk = std::max<int64_t>(1, std::min<int64_t>(64, (int64_t)(((size_t)16 << 30) / inter_pp)));
+    g->chunk = chunk;
+    int rc = dev_alloc(&g->d_inter, inter_pp * (size_t)chunk, "group intermediate transform");
+    if (!rc) rc = dev_alloc(&g->d_partials, sizeof(Partial) * (size_t)chunk * nb, "group argmax partials");
+    if (!rc) {
+        cudaError_t e = cudaStreamCreateWithFlags(&g->st, cudaStreamNonBlocking);
+        if (e != cudaSuccess) rc = fail(FCAS_ERR_CUDA, "fcas_group_create: %s", cudaGetErrorString(e));
+    }
+    if (rc) {
+        fcas_group_destroy(g);
+        return rc;
+    }
+    *out = g;
+    return FCAS_OK;
+}
+
+int fcas_group_search(fcas_group* g, const fcas_pso_config* cfg, fcas_search_result* results, void* stream) {
+    g_last_error.clear();
+    if (!g || !results) return fail(FCAS_ERR_INVALID, "fcas_group_search: NULL argument");
+    char msg[256];
+    int rc = pso_validate(cfg, msg, sizeof(msg));
+    if (rc) return fail(rc, "fcas_group_search: %s", msg);
+    const int n_ctx = (int)g->ctxs.size();
+    const int64_t rows = (int64_t)cfg->n_runs * cfg->n_particles;
+    if (rows > g->params_cap) {
+        if (g->d_params) cudaFree(g->d_params);
+        g->d_params = nullptr;
+        g->params_cap = 0;
+        rc = dev_alloc(&g->d_params, sizeof(ParticleParams) * (size_t)rows, "group particle parameters");
+        if (rc) return rc;
+        g->params_cap = rows;
+    }
+    const size_t per = align256(swarm_bytes(rows, cfg->n_runs));
+    if (per * n_ctx > g->pso_bytes) {
+        if (g->d_pso) cudaFree(g->d_pso);
+        g->d_pso = nullptr;
+        g->pso_bytes = 0;
+        rc = dev_alloc(&g->d_pso, per * n_ctx, "group swarm state");
+        if (rc) return rc;
+        g->pso_bytes = per * n_ctx;
+    }
+    std::vector<Swarm> ws(n_ctx);
+    std::vector<PsoDev> gs(n_ctx);
+    for (int i = 0; i < n_ctx; ++i) {
+        ws[i] = carve_swarm(g->d_pso + per * i, rows, cfg->n_runs);
+        fcas_pso_config ci = *cfg;
+        ci.seed = segment_seed(cfg->seed, i);
+        gs[i] = pso_dev(&ci);
+    }
+    cudaStream_t st = g->st;
+    cudaEvent_t ev;
+    FCAS_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    cudaEventRecord(ev, static_cast<cudaStream_t>(stream));
+    cudaStreamWaitEvent(st, ev, 0);
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < n_ctx && e == cudaSuccess; ++i) e = launch_pso_init(gs[i], ws[i].s, st);
+    if (e == cudaSuccess)
+        e = run_iterations(cfg->n_iter, st, [&]() {
+            cudaError_t x = cudaSuccess;
+            for (int i = 0; i < n_ctx && x == cudaSuccess; ++i)
+                x = swarm_iteration(g->ctxs[i], gs[i], ws[i], g->d_params, g->d_inter, g->d_partials, g->chunk, rows,
+                                    st);
+            return x;
+        });
+    for (int i = 0; i < n_ctx && e == cudaSuccess; ++i) {
+        e = launch_pso_result(gs[i], ws[i].s, ws[i].res, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(results + (size_t)i * cfg->n_runs, ws[i].res, sizeof(fcas_search_result) * cfg->n_runs,
+                                cudaMemcpyDeviceToHost, st);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaEventDestroy(ev);
+    if (e != cudaSuccess) return fail(FCAS_ERR_CUDA, "fcas_group_search: %s", cudaGetErrorString(e));
+    return FCAS_OK;
+}
+
+void fcas_group_destroy(fcas_group* g) {
+    if (!g) return;
+    cudaDeviceSynchronize();
+    void* ptrs[] = {g->d_inter, g->d_partials, g->d_params, g->d_pso};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (g->st) cudaStreamDestroy(g->st);
+    delete g;
 }
 
 int fcas_gradient(fcas_ctx* c, int64_t n, const double* theta, const int64_t* tc, double* grad, void* stream) {
@@ -529,7 +854,7 @@ int fcas_gradient(fcas_ctx* c, int64_t n, const double* theta, const int64_t* tc
     FCAS_CUDA(launch_geometry(d_theta, n, c->d_params, c->d_det, c->d_sigma2s, c->setup.n_det, c->setup.f_low, c->df,
                               st));
     const FitnessPlan plan = make_plan(c);
-    const int k1b = pass_a_k1b_for(c->log_n2, c->setup.precision);
+    const int k1b = c->k1b;
     if (c->setup.precision == FCAS_PREC_FP32)
         FCAS_CUDA(launch_grad_sums<float>(plan, k1b, c->k_lo, c->k_hi, c->d_params, d_tc, n, c->d_gsums, st));
     else
@@ -565,6 +890,10 @@ int fcas_get_info(const fcas_ctx* c, fcas_info* info) {
     for (int i = 0; i < c->setup.n_det; ++i) info->sigma2[i] = c->sigma2[i];
     info->inter_bytes = (int64_t)inter_bytes_per_particle(c->setup.precision, c->setup.n_fft);
     info->series = kSeries;
+    info->split_bias = c->split_bias;
+    info->k1b = c->k1b;
+    info->sub = c->sub;
+    info->tuned_ms_per_particle = c->tuned_ms;
     return FCAS_OK;
 }
 

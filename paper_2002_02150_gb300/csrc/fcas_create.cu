@@ -219,45 +219,68 @@ cudaError_t launch_data_fft(const double* data, int n_det, int64_t n_samples, in
 }
 
 // ------------------------------------------------------------------------------------------
-// Y_i[k] = s 4 df f_k^{-7/6} e^{-i pi/4} dt X~_i[k] / S_i[k] on the band (zero elsewhere), laid out
-// as [k1 / K1B][i][k2 < N2/2][k1 % K1B] with k = k1 + N1 k2 (one detector's rows of a block adjacent),
-// and the float-float chirp basis phi^-5/3, phi^-1, phi^-2/3, phi^-1/3 (phi = f_k / f_*) in the
-// order [k1 / K1B][k2][k1 % K1B].
+// Over-whitening (Sec. II.D) into the natural-order band spectrum kept by the context:
+// ynat_i[k] = s 4 df f_k^{-7/6} e^{-i pi/4} dt X~_i[k] / S_i[k] for k in the band, 0 elsewhere
+// (k < N/2; s the power-of-two scale).
 // ------------------------------------------------------------------------------------------
-__global__ void prep_kernel(const double2* __restrict__ spec, const double* __restrict__ psd, int n_det,
-                            int64_t psd_row, int log_n, int log_n1, int log_n2, int k1b, int64_t k_lo, int64_t k_hi,
-                            double fs, double f_star, double scale, int precision, void* __restrict__ y,
-                            void* __restrict__ basis) {
+__global__ void whiten_kernel(const double2* __restrict__ spec, const double* __restrict__ psd, int n_det,
+                              int64_t psd_row, int log_n, int64_t k_lo, int64_t k_hi, double fs, double scale,
+                              double2* __restrict__ ynat) {
     const int64_t n = (int64_t)1 << log_n;
+    const int64_t half = n / 2;
+    const double df = fs / (double)n;
+    const double dt = 1.0 / fs;
+    const double rs2 = 0.70710678118654752440;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < half * n_det;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(g / half);
+        const int64_t k = g % half;
+        double2 yv = make_double2(0.0, 0.0);
+        if (k >= k_lo && k <= k_hi) {
+            const double f = (double)k * df;
+            const double2 x = spec[(int64_t)i * n + k];
+            const double a = scale * 4.0 * df * pow(f, -7.0 / 6.0) * dt / psd[i * psd_row + k];
+            // (x.re + i x.im) (1 - i) / sqrt 2
+            yv = make_double2(a * rs2 * (x.x + x.y), a * rs2 * (x.y - x.x));
+        }
+        ynat[g] = yv;
+    }
+}
+
+cudaError_t launch_whiten(const double2* spec, const double* psd, int n_det, int64_t psd_row, int log_n, int64_t k_lo,
+                          int64_t k_hi, double fs, double scale, double2* ynat, cudaStream_t s) {
+    whiten_kernel<<<4096, 256, 0, s>>>(spec, psd, n_det, psd_row, log_n, k_lo, k_hi, fs, scale, ynat);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------
+// Layout of the spectrum for pass A: Y as [k1 / K1B][i][k2 < N2/2][k1 % K1B] with k = k1 + N1 k2 (one
+// detector's rows of a block adjacent), and the chirp basis phi^-5/3, phi^-1, phi^-2/3, phi^-1/3
+// (phi = f_k / f_*) in the order [k1 / K1B][k2][k1 % K1B] (float-float pairs in the FP32 form).
+// ------------------------------------------------------------------------------------------
+__global__ void layout_kernel(const double2* __restrict__ ynat, int n_det, int log_n, int log_n1, int log_n2, int k1b,
+                              int64_t k_lo, int64_t k_hi, double fs, double f_star, int precision,
+                              void* __restrict__ y, void* __restrict__ basis) {
+    const int64_t n = (int64_t)1 << log_n;
+    const int64_t half = n / 2;
     const int64_t n1 = (int64_t)1 << log_n1;
     const int64_t half2 = ((int64_t)1 << log_n2) / 2;
     const int64_t total = n1 * half2;
     const double df = fs / (double)n;
-    const double dt = 1.0 / fs;
-    const double rs2 = 0.70710678118654752440;
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
         const int64_t c = g % k1b;
         const int64_t k2 = (g / k1b) % half2;
         const int64_t blk = g / (k1b * half2);
         const int64_t k = blk * k1b + c + n1 * k2;
-        const bool in_band = k >= k_lo && k <= k_hi;
-        const double f = (double)k * df;
         for (int i = 0; i < n_det; ++i) {
-            double2 yv = make_double2(0.0, 0.0);
-            if (in_band) {
-                const double2 x = spec[(int64_t)i * n + k];
-                const double a = scale * 4.0 * df * pow(f, -7.0 / 6.0) * dt / psd[i * psd_row + k];
-                // (x.re + i x.im) (1 - i) / sqrt 2
-                yv = make_double2(a * rs2 * (x.x + x.y), a * rs2 * (x.y - x.x));
-            }
-            // detector-major inside each block of K1B columns: [blk][i][k2][c]
+            const double2 yv = ynat[(int64_t)i * half + k];
             const int64_t yi = ((blk * n_det + i) * half2 + k2) * k1b + c;
             if (precision == FCAS_PREC_FP32) static_cast<float2*>(y)[yi] = make_float2((float)yv.x, (float)yv.y);
             else static_cast<double2*>(y)[yi] = yv;
         }
         double b53 = 0.0, b1 = 0.0, b23 = 0.0, b13 = 0.0;
-        if (in_band) {
-            b1 = f_star / f;
+        if (k >= k_lo && k <= k_hi) {
+            b1 = f_star / ((double)k * df);
             b13 = cbrt(b1);
             b23 = b13 * b13;
             b53 = b1 * b23;
@@ -277,13 +300,11 @@ __global__ void prep_kernel(const double2* __restrict__ spec, const double* __re
     }
 }
 
-cudaError_t launch_prep(const double2* spec, const double* psd, int n_det, int64_t psd_row, int log_n, int log_n1,
-                        int log_n2, int64_t k_lo, int64_t k_hi, double fs, double f_star, double scale, int precision,
-                        void* y, void* basis, cudaStream_t s) {
-    const int k1b = pass_a_k1b_for(log_n2, precision);
+cudaError_t launch_layout(const double2* ynat, int n_det, int log_n, int log_n1, int log_n2, int k1b, int64_t k_lo,
+                          int64_t k_hi, double fs, double f_star, int precision, void* y, void* basis, cudaStream_t s) {
     if (k1b <= 0) return cudaErrorInvalidValue;
-    prep_kernel<<<4096, 256, 0, s>>>(spec, psd, n_det, psd_row, log_n, log_n1, log_n2, k1b, k_lo, k_hi, fs, f_star,
-                                     scale, precision, y, basis);
+    layout_kernel<<<4096, 256, 0, s>>>(ynat, n_det, log_n, log_n1, log_n2, k1b, k_lo, k_hi, fs, f_star, precision, y,
+                                       basis);
     return cudaGetLastError();
 }
 

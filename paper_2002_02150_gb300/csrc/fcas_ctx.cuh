@@ -31,6 +31,12 @@ struct fcas_ctx {
     double sigma2[FCAS_MAX_DET] = {};
     double* d_det = nullptr;        // [D][9]
     double* d_sigma2s = nullptr;    // scaled template norms
+    double2* d_ynat = nullptr;      // whitened band spectrum in natural order [D][N/2] (binary64)
+    int split_bias = 0;             // N2 = 2^(floor(log2 N / 2) - split_bias)
+    int k1b = 0;                    // pass-A columns per CTA (layout of d_y and d_basis)
+    int sub = 8;                    // pass-A column blocks scheduled together
+    double tuned_ms = 0.0;          // per-particle time of the tuned configuration (0: not tuned)
+    int64_t nb_cap = 0;             // argmax partials per particle the scratch holds
     void* d_y = nullptr;            // Y (precision-dependent)
     void* d_basis = nullptr;
     void* d_tw = nullptr;           // precision-dependent copies of the twiddle tables
@@ -85,6 +91,8 @@ inline FitnessPlan make_plan(const fcas_ctx* c) {
     p.basis = c->d_basis;
     p.stw_a = fp32 ? (const void*)c->d_stw_a32 : (const void*)c->d_stw_a64;
     p.stw_b = fp32 ? (const void*)c->d_stw_b32 : (const void*)c->d_stw_b64;
+    p.k1b = c->k1b;
+    p.sub = c->sub;
     p.tw_lo = c->d_twlo;
     p.tw_hi = c->d_twhi;
     return p;

@@ -108,8 +108,8 @@ constexpr int kSeries = 2;
 constexpr int kMinLogN = 4;
 constexpr int kMaxLogN = 24;
 constexpr int kMaxLogPass = 13;
-__host__ __device__ constexpr int split_log_n2(int log_n) {
-    return imax_c(2, imax_c(log_n - kMaxLogPass, log_n / 2 - FCAS_SPLIT_BIAS));
+__host__ __device__ constexpr int split_log_n2_with(int log_n, int bias) {
+    return imax_c(2, imax_c(log_n - kMaxLogPass, log_n / 2 - bias));
 }
 
 }  // namespace fcas

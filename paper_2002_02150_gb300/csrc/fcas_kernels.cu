@@ -182,17 +182,16 @@ struct DetConst {
     Real dh[FCAS_MAX_DET], dl[FCAS_MAX_DET], w1[FCAS_MAX_DET], w2[FCAS_MAX_DET];
 };
 
-template <typename Real, int LOG_L>
-__global__ void __launch_bounds__(pass_a_threads(LOG_L, sizeof(Real)), 1)
+template <typename Real, int LOG_L, int K1B>
+__global__ void __launch_bounds__(K1B * ((1 << LOG_L) / shape_v(LOG_L)), 1)
 pass_a_kernel(const cplx<Real>* __restrict__ y, const Basis<Real>* __restrict__ basis,
-              const ParticleParams* __restrict__ params, int64_t p0, int64_t np, int n_det, int log_n1,
+              const ParticleParams* __restrict__ params, int64_t p0, int64_t np, int n_det, int log_n1, int sub_req,
               cplx<Real>* __restrict__ out, const cplx<Real>* __restrict__ stw,
               const cplx<Real>* __restrict__ tw_lo, const cplx<Real>* __restrict__ tw_hi) {
     using C = cplx<Real>;
     constexpr int L = 1 << LOG_L;
     constexpr int V = shape_v(LOG_L);
     constexpr int G = L / V;
-    constexpr int K1B = pass_a_k1b(LOG_L, sizeof(Real));
     constexpr int VH = V / 2;    // values with k2 < L/2; the rest of the column is zero (k >= N/2)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* smem = reinterpret_cast<C*>(smem_raw);
@@ -205,7 +204,7 @@ pass_a_kernel(const cplx<Real>* __restrict__ y, const Basis<Real>* __restrict__ 
     // together (so L2 merges them before write-back) and the chunk's particles read the same
     // spectrum block close in time (so it is fetched from DRAM once).
     const int nblk = (1 << log_n1) / K1B;
-    const int sub = FCAS_PASS_A_SUB < nblk ? FCAS_PASS_A_SUB : nblk;
+    const int sub = sub_req < nblk ? sub_req : nblk;
     const int64_t lin = blockIdx.x;
     const int64_t rest = lin / sub;
     const int64_t p = rest % np;
@@ -468,22 +467,63 @@ int pass_b_blocks_per_particle(int log_n1, int log_n2, int precision) {
     }
 }
 
-template <typename Real, int LG>
+template <typename Real, int LG, int K1B>
 static cudaError_t pass_a_at(const FitnessPlan& pl, const ParticleParams* params, int64_t p0, int64_t np, void* inter,
                              cudaStream_t s) {
-    constexpr int K1B = pass_a_k1b(LG, sizeof(Real));
-    constexpr int THREADS = pass_a_threads(LG, sizeof(Real));
+    constexpr int THREADS = K1B * ((1 << LG) / shape_v(LG));
     const size_t smem = sizeof(cplx<Real>) * (size_t)K1B * fft16_buf_elems(LG);
-    auto kern = pass_a_kernel<Real, LG>;
+    auto kern = pass_a_kernel<Real, LG, K1B>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t ctas = np * ((1 << pl.log_n1) / K1B);
     kern<<<(unsigned)ctas, THREADS, smem, s>>>(static_cast<const cplx<Real>*>(pl.y),
                                      static_cast<const Basis<Real>*>(pl.basis),
-                                     params, p0, np, pl.n_det, pl.log_n1, static_cast<cplx<Real>*>(inter),
+                                     params, p0, np, pl.n_det, pl.log_n1, pl.sub, static_cast<cplx<Real>*>(inter),
                                      static_cast<const cplx<Real>*>(pl.stw_a), static_cast<const cplx<Real>*>(pl.tw_lo),
                                      static_cast<const cplx<Real>*>(pl.tw_hi));
     return cudaGetLastError();
+}
+
+// Column-block widths compiled for pass A: the default of the length and, for the FP32 form at
+// lengths >= 2^8, half and twice it (the autotuner's choices).
+template <int LG, int RB>
+constexpr bool k1b_variant_ok(int k) {
+    return k >= 1 && k <= 16 && k <= (1 << LG) && k * ((1 << LG) / shape_v(LG)) <= 1024;
+}
+
+template <typename Real, int LG>
+static cudaError_t pass_a_lg(const FitnessPlan& pl, const ParticleParams* params, int64_t p0, int64_t np,
+                             void* inter, cudaStream_t s) {
+    constexpr int RB = sizeof(Real);
+    constexpr int KD = pass_a_k1b(LG, RB);
+    if (pl.k1b == KD) return pass_a_at<Real, LG, KD>(pl, params, p0, np, inter, s);
+    if constexpr (RB == 4 && LG >= 8) {
+        if constexpr (k1b_variant_ok<LG, RB>(KD / 2))
+            if (pl.k1b == KD / 2) return pass_a_at<Real, LG, (KD / 2 > 0 ? KD / 2 : 1)>(pl, params, p0, np, inter, s);
+        if constexpr (k1b_variant_ok<LG, RB>(KD * 2))
+            if (pl.k1b == KD * 2) return pass_a_at<Real, LG, (KD * 2 <= 16 ? KD * 2 : 16)>(pl, params, p0, np, inter, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+int pass_a_k1b_variants(int log_n2, int precision, int* out) {
+    const int rb = precision == FCAS_PREC_FP32 ? 4 : 8;
+    int n = 0;
+    switch (log_n2) {
+#define FCAS_CASE(LG)                                                                       \
+    case LG: {                                                                              \
+        const int kd = pass_a_k1b(LG, rb);                                                  \
+        out[n++] = kd;                                                                      \
+        if (rb == 4 && LG >= 8) {                                                           \
+            if (k1b_variant_ok<LG, 4>(kd / 2)) out[n++] = kd / 2;                           \
+            if (k1b_variant_ok<LG, 4>(kd * 2)) out[n++] = kd * 2;                           \
+        }                                                                                   \
+        return n;                                                                           \
+    }
+        FCAS_LOG_CASES(FCAS_CASE)
+#undef FCAS_CASE
+        default: return 0;
+    }
 }
 
 template <typename Real, int LG>
@@ -506,7 +546,7 @@ cudaError_t launch_pass_a(const FitnessPlan& pl, const ParticleParams* params, i
                           cudaStream_t s) {
     if (np <= 0) return cudaSuccess;
     switch (pl.log_n2) {
-#define FCAS_CASE(LG) case LG: return pass_a_at<Real, LG>(pl, params, p0, np, inter, s);
+#define FCAS_CASE(LG) case LG: return pass_a_lg<Real, LG>(pl, params, p0, np, inter, s);
         FCAS_LOG_CASES(FCAS_CASE)
 #undef FCAS_CASE
         default: return cudaErrorInvalidValue;

@@ -33,6 +33,8 @@ struct FitnessPlan {
     const void* basis;            // basis layout [k1 / K1B][k2 < N2/2][k1 % K1B]
     const void* stw_a;            // per-stage twiddles of the length-N2 transforms
     const void* stw_b;            // per-stage twiddles of the length-N1 transforms
+    int k1b;                      // columns per pass-A CTA (must match the layout of y and basis)
+    int sub;                      // adjacent column blocks of a particle scheduled together
     const void* tw_lo;            // e^{2 pi i m / N}, m < 4096
     const void* tw_hi;            // e^{2 pi i 4096 m / N}, m < max(1, N / 4096)
 };
@@ -56,6 +58,8 @@ cudaError_t launch_reduce(const Partial* partials, int64_t nb, const ParticlePar
 
 int pass_b_blocks_per_particle(int log_n1, int log_n2, int precision);
 int pass_a_k1b_for(int log_n2, int precision);
+// compiled pass-A column-block widths for a length: writes up to 3 values, returns the count
+int pass_a_k1b_variants(int log_n2, int precision, int* out);
 cudaError_t launch_stage_tables(int log_l, double2* t64, float2* t32, cudaStream_t s);
 
 // ---- adjoint (fcas_grad.cu) ----
@@ -77,8 +81,9 @@ cudaError_t launch_sigma2(const double* psd, int n_det, int64_t row, int64_t k_l
 cudaError_t launch_data_fft(const double* data, int n_det, int64_t n_samples, int log_n, int log_n1, int log_n2,
                             const double2* tw64, int tw_shift_a, int tw_shift_b, const double2* twlo64,
                             const double2* twhi64, double2* work, double2* spec, cudaStream_t s);
-cudaError_t launch_prep(const double2* spec, const double* psd, int n_det, int64_t psd_row, int log_n, int log_n1,
-                        int log_n2, int64_t k_lo, int64_t k_hi, double fs, double f_star, double scale,
-                        int precision, void* y, void* basis, cudaStream_t s);
+cudaError_t launch_whiten(const double2* spec, const double* psd, int n_det, int64_t psd_row, int log_n, int64_t k_lo,
+                          int64_t k_hi, double fs, double scale, double2* ynat, cudaStream_t s);
+cudaError_t launch_layout(const double2* ynat, int n_det, int log_n, int log_n1, int log_n2, int k1b, int64_t k_lo,
+                          int64_t k_hi, double fs, double f_star, int precision, void* y, void* basis, cudaStream_t s);
 
 }  // namespace fcas

@@ -33,7 +33,7 @@ class fcas_detector(ctypes.Structure):
 class fcas_setup(ctypes.Structure):
     _fields_ = [("n_det", ctypes.c_int32), ("precision", ctypes.c_int32), ("n_samples", ctypes.c_int64),
                 ("n_fft", ctypes.c_int64), ("fs", ctypes.c_double), ("f_low", ctypes.c_double),
-                ("f_high", ctypes.c_double), ("max_batch", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("f_high", ctypes.c_double), ("max_batch", ctypes.c_int32), ("flags", ctypes.c_int32)]
 
 
 class fcas_info(ctypes.Structure):
@@ -41,7 +41,9 @@ class fcas_info(ctypes.Structure):
                 ("k_lo", ctypes.c_int64), ("k_hi", ctypes.c_int64), ("n_band", ctypes.c_int64),
                 ("chunk", ctypes.c_int64), ("n_det", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("scale", ctypes.c_double), ("sigma2", ctypes.c_double * FCAS_MAX_DET),
-                ("inter_bytes", ctypes.c_int64), ("series", ctypes.c_int64)]
+                ("inter_bytes", ctypes.c_int64), ("series", ctypes.c_int64), ("split_bias", ctypes.c_int32),
+                ("k1b", ctypes.c_int32), ("sub", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("tuned_ms_per_particle", ctypes.c_double)]
 
 
 class fcas_pso_config(ctypes.Structure):
@@ -102,6 +104,16 @@ def load_library():
     lib.fcas_search.restype = i32
     lib.fcas_gradient.argtypes = [vp, i64, vp, vp, vp, vp]
     lib.fcas_gradient.restype = i32
+    lib.fcas_autotune.argtypes = [vp, i64, ctypes.c_char_p, vp]
+    lib.fcas_autotune.restype = i32
+    lib.fcas_set_shape.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, vp]
+    lib.fcas_set_shape.restype = i32
+    lib.fcas_group_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int32, ctypes.POINTER(vp), ctypes.c_int32]
+    lib.fcas_group_create.restype = i32
+    lib.fcas_group_search.argtypes = [vp, ctypes.POINTER(fcas_pso_config), ctypes.POINTER(fcas_search_result), vp]
+    lib.fcas_group_search.restype = i32
+    lib.fcas_group_destroy.argtypes = [vp]
+    lib.fcas_group_destroy.restype = None
     _lib = lib
     return lib
 
@@ -166,7 +178,10 @@ class Context:
         self.close()
 
 
-def fcas_create(det, psd, data, n_fft, fs, f_low, f_high, precision="fp32", max_batch=0, stream=None):
+FCAS_SETUP_LAZY_SCRATCH = 1
+
+
+def fcas_create(det, psd, data, n_fft, fs, f_low, f_high, precision="fp32", max_batch=0, stream=None, flags=0):
     """Prepare a data segment. det: (D, 9) ECEF r, x arm, y arm; psd: (D, n_fft/2+1); data: (D, n_samples)."""
     lib = load_library()
     det = np.asarray(det, dtype=np.float64).reshape(-1, 9)
@@ -178,7 +193,8 @@ def fcas_create(det, psd, data, n_fft, fs, f_low, f_high, precision="fp32", max_
         dets[i].yarm[:] = det[i, 6:9]
     n_samples = int(data.shape[-1])
     prec = {"fp32": FCAS_PREC_FP32, "fp64": FCAS_PREC_FP64}[precision] if isinstance(precision, str) else int(precision)
-    setup = fcas_setup(n_det, prec, n_samples, int(n_fft), float(fs), float(f_low), float(f_high), int(max_batch), 0)
+    setup = fcas_setup(n_det, prec, n_samples, int(n_fft), float(fs), float(f_low), float(f_high), int(max_batch),
+                       int(flags))
     p_psd, k1 = _ptr(psd, np.float64)
     p_data, k2 = _ptr(data, np.float64)
     handle = ctypes.c_void_p()
@@ -366,3 +382,62 @@ def polish(ctx, theta, steps=10, scales=(1e-2, 1e-2, 1e-4, 1e-4), judge=None, ma
             done |= ok
             step[~done] *= 0.5
     return theta, fit, accepted
+
+
+def fcas_autotune(ctx, n_particles=64, cache_path=None, stream=None):
+    """Time the launch shapes on this context and keep the fastest; returns fcas_get_info(ctx)."""
+    path = cache_path.encode() if cache_path else None
+    s = ctypes.c_void_p(int(stream)) if stream is not None else ctypes.c_void_p(0)
+    _check(load_library().fcas_autotune(ctx.handle, int(n_particles), path, s))
+    return fcas_get_info(ctx)
+
+
+def fcas_set_shape(ctx, split_bias=0, k1b=0, sub=8, stream=None):
+    s = ctypes.c_void_p(int(stream)) if stream is not None else ctypes.c_void_p(0)
+    _check(load_library().fcas_set_shape(ctx.handle, int(split_bias), int(k1b), int(sub), s))
+    return fcas_get_info(ctx)
+
+
+class Group:
+    """Owns one fcas_group (segments searched together with shared scratch)."""
+
+    def __init__(self, contexts, max_batch=0):
+        self.contexts = list(contexts)           # keep the contexts alive as long as the group
+        arr = (ctypes.c_void_p * len(self.contexts))(*[c.handle for c in self.contexts])
+        self.handle = ctypes.c_void_p()
+        _check(load_library().fcas_group_create(ctypes.byref(self.handle), len(self.contexts), arr, int(max_batch)))
+
+    def search(self, cfg, stream=None):
+        """Returns a list (per segment) of lists (per run) of result dicts."""
+        n = len(self.contexts)
+        res = (fcas_search_result * (n * cfg.n_runs))()
+        s = ctypes.c_void_p(int(stream)) if stream is not None else ctypes.c_void_p(0)
+        _check(load_library().fcas_group_search(self.handle, ctypes.byref(cfg), res, s))
+        out = [dict(fitness=r.fitness, theta=list(r.theta), tc=r.tc, evaluations=r.evaluations) for r in res]
+        return [out[i * cfg.n_runs:(i + 1) * cfg.n_runs] for i in range(n)]
+
+    def close(self):
+        if self.handle:
+            load_library().fcas_group_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def fcas_group_create(contexts, max_batch=0):
+    return Group(contexts, max_batch)
+
+
+def segment_seed(seed, s):
+    """Key of segment s's swarm in a group search (seed + s * 0x9E3779B97F4A7C15 mod 2^64)."""
+    return (int(seed) + s * 0x9E3779B97F4A7C15) & 0xFFFFFFFFFFFFFFFF

@@ -58,7 +58,7 @@ def test_struct_layouts_match_header(tmp_path):
 
 def _bad_create(lib, **over):
     import paper_2002_02150_gb300.fcas as f
-    s = dict(n_det=2, precision=1, n_samples=64, n_fft=64, fs=64.0, f_low=4.0, f_high=20.0, max_batch=0, reserved=0)
+    s = dict(n_det=2, precision=1, n_samples=64, n_fft=64, fs=64.0, f_low=4.0, f_high=20.0, max_batch=0, flags=0)
     s.update(over)
     setup = f.fcas_setup(**s)
     dets = (f.fcas_detector * 2)()
@@ -76,7 +76,7 @@ def _bad_create(lib, **over):
     (dict(n_fft=100), "power of two"), (dict(n_fft=8, n_samples=8), "power of two"),
     (dict(n_samples=65), "n_samples"), (dict(n_samples=0), "n_samples"), (dict(fs=0.0), "fs"),
     (dict(f_low=0.0), "f_low"), (dict(f_low=30.0, f_high=20.0), "f_low"), (dict(f_low=31.9, f_high=40.0), "band"),
-    (dict(reserved=1), "reserved"),
+    (dict(flags=6), "flags"),
 ])
 def test_create_rejects_invalid_setup(lib, over, needle):
     rc, msg = _bad_create(lib, **over)
