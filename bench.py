@@ -12,6 +12,7 @@ its own data realisation and particle batch, no data-path collective).
 """
 
 import argparse
+import dataclasses
 import glob
 import hashlib
 import json
@@ -47,6 +48,9 @@ def parse():
     ap.add_argument("--max-batch", type=int, default=0, help="particles per internal chunk (0 = automatic)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
     ap.add_argument("--no-search", action="store_true", help="skip the PSO search measurements")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default launch shape (no autotuning)")
+    ap.add_argument("--group-segments", type=int, default=6,
+                    help="segments of the batched uneven-length measurement (0 = skip)")
     return ap.parse_args()
 
 
@@ -184,6 +188,8 @@ def bench_ours(args, ranks):
     n = theta.shape[0]
     ctx = fc.fcas_create(data["det"], data["psd"], data["data"], w.n_fft, w.fs, w.f_low, w.f_high, precision="fp32",
                          max_batch=args.max_batch)
+    if not args.no_tune:
+        fc.fcas_autotune(ctx, min(64, n))
     info = fc.fcas_get_info(ctx)
     th = torch.tensor(theta, device=dev)
     fit = torch.empty(n, dtype=torch.float64, device=dev)
@@ -279,6 +285,7 @@ def bench_ours(args, ranks):
         ctx64.close()
 
     search = None if args.no_search else bench_search(fc, ranks, data, w, dev)
+    group = None if args.group_segments <= 0 else bench_group(fc, ranks, args.group_segments, dev)
 
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": ranks.world, "steps": args.steps,
@@ -287,6 +294,8 @@ def bench_ours(args, ranks):
         "config": {"workload": w.name, "detectors": list(w.detectors), "n_fft": w.n_fft, "n_samples": w.n_samples,
                    "fs": w.fs, "band_hz": [w.f_low, w.f_high], "particles_per_gpu": n,
                    "precision": "fp32 + float-float phase", "chunk": info["chunk"],
+                   "shape": {"split_bias": info["split_bias"], "k1b": info["k1b"], "sub": info["sub"],
+                             "autotuned": info["tuned_ms_per_particle"] > 0},
                    "l2": "inputs larger than L2 (intermediate %.1f GB per step), no flush" % (n * info["inter_bytes"] / 1e9)},
         "roofline": roofline, "kernels": kernels, "gpu_launches": gpu_launches, "e2e": e2e, "clocks": clock,
         "fp64_form": fp64,
@@ -294,6 +303,7 @@ def bench_ours(args, ranks):
                                        {"value": round(PSO_EVALS / value / DATA_SECONDS, 5),
                                         "how": "extrapolated: 8 runs x 40 particles x 2000 iterations / value / 3600 s"}),
         "search": search["search_64s"] if search else None,
+        "batched_uneven": group,
         "paper_context": {"search_over_data": [1.4, 0.5], "hardware": "1 KNL node per PSO run, FP64"},
     }
     if ranks.rank == 0 and args.cpu_sample > 0:
@@ -355,6 +365,45 @@ def bench_search(fc, ranks, data60, w60, dev):
                                            "how": f"60-min data, 8 runs x 40 particles: {iters} iterations measured "
                                                   f"in {wall:.3f} s, scaled linearly to 2000 iterations",
                                            "search_s_2000_iterations": round(scaled, 2)}}
+
+
+def bench_group(fc, ranks, n_seg, dev, iters=5):
+    """Uneven batching: n_seg noise realisations with DNS injections (SNR ~ U[10, 14], masses ~ U[1, 3]
+    Msun, random sky), durations cycled over 15/30/60 min at 2048 Hz (FFT lengths 2^21, 2^22, 2^23),
+    every segment's swarm (8 runs x 40 particles) advanced together, one graph launch per iteration,
+    each segment with autotuned launch shapes."""
+    import tempfile
+    import torch
+    rng = np.random.default_rng(4000 + ranks.rank)
+    cache = os.path.join(tempfile.gettempdir(), f"fcas_tune_rank{ranks.rank}.txt")
+    ctxs, lengths = [], []
+    for s_ in range(n_seg):
+        minutes, n_fft = ((15, 1 << 21), (30, 1 << 22), (60, 1 << 23))[s_ % 3]
+        n_samples = minutes * 60 * 2048
+        m1, m2 = rng.uniform(1.0, 3.0, 2)
+        w = dataclasses.replace(sd.C2, name=f"{minutes}min", n_samples=n_samples, n_fft=n_fft, m1=m1, m2=m2,
+                                snr=float(rng.uniform(10.0, 14.0)), arrival_s=n_samples / 2048.0 / 3.0)
+        d = sd.make_dataset(w, seed=500 + 64 * ranks.rank + s_)
+        ctx = fc.fcas_create(d["det"], d["psd"], d["data"], w.n_fft, w.fs, w.f_low, w.f_high,
+                             flags=fc.FCAS_SETUP_LAZY_SCRATCH)
+        fc.fcas_autotune(ctx, 64, cache)
+        ctxs.append(ctx)
+        lengths.append(n_fft)
+    cfg = lambda it: fc.pso_config(n_runs=8, n_particles=40, n_iter=it, seed=7, box=_pso_box(sd.C2))
+    with fc.fcas_group_create(ctxs) as grp:
+        grp.search(cfg(2))                      # warm-up (also builds the iteration graph once)
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter()
+        res = grp.search(cfg(iters))
+        wall = time.perf_counter() - t
+    shapes = [fc.fcas_get_info(c) for c in ctxs]
+    for c in ctxs:
+        c.close()
+    evals = sum(r["evaluations"] for seg in res for r in seg)
+    return {"segments": n_seg, "fft_lengths": lengths, "runs_per_segment": 8, "particles": 40, "iterations": iters,
+            "wall_s": round(wall, 4), "s_per_iteration": round(wall / iters, 5),
+            "evals_per_s": round(evals / wall, 1), "evaluations": int(evals),
+            "shapes": [{k: i[k] for k in ("n_fft", "split_bias", "k1b", "sub")} for i in shapes]}
 
 
 def cpu_baseline(w, data, theta, sample):

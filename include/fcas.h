@@ -219,8 +219,8 @@ int fcas_gradient(fcas_ctx* ctx, int64_t n, const double* theta, const int64_t* 
 /*
  * fcas_autotune -- choose the launch shapes of the fitness path for this context by timing them:
  * the N = n1 n2 split (balanced, or a pass-A transform half as long), the number of columns per
- * pass-A CTA among the compiled widths, and how many adjacent column blocks of a particle are
- * scheduled together (1, 4, 8, 16). Each candidate evaluates n_particles particles (one warm-up,
+ * pass-A CTA among the compiled widths, pass A's stage radix (16, or 8 with twice the threads),
+ * and how many adjacent column blocks of a particle are scheduled together (1, 4, 8, 16). Each candidate evaluates n_particles particles (one warm-up,
  * three timed launches, CUDA events); the fastest is kept (the spectrum is laid out again for it).
  * cache_path (may be NULL): a text file of earlier results keyed by GPU name, n_fft, n_det,
  * precision and n_particles; a hit is applied without timing, a miss is timed and appended.
@@ -239,10 +239,11 @@ typedef struct fcas_group fcas_group;
 
 /*
  * fcas_set_shape -- pin the launch shape without timing: split_bias 0 or 1, k1b one of the compiled
- * pass-A widths for the resulting length (0 = default), sub a power of two. FCAS_ERR_INVALID for a
- * shape that is not available. Synchronous.
+ * pass-A widths for the resulting length (0 = default), sub a power of two, radix_bits_a 4 (radix-16
+ * stages; 0 means 4) or 3 (radix-8 stages, FP32 form, 2^10..2^12-point columns, k1b = 4).
+ * FCAS_ERR_INVALID for a shape that is not available. Synchronous.
  */
-int fcas_set_shape(fcas_ctx* ctx, int32_t split_bias, int32_t k1b, int32_t sub, void* stream);
+int fcas_set_shape(fcas_ctx* ctx, int32_t split_bias, int32_t k1b, int32_t sub, int32_t radix_bits_a, void* stream);
 
 /* max_batch: particles per chunk of the shared scratch (0 = automatic, <= 64). */
 int fcas_group_create(fcas_group** out, int32_t n_ctx, fcas_ctx* const* ctxs, int32_t max_batch);
@@ -279,7 +280,7 @@ typedef struct fcas_info {
     int32_t split_bias;         /* n2 = 2^(floor(log2 n_fft / 2) - split_bias) */
     int32_t k1b;                /* pass-A columns per CTA */
     int32_t sub;                /* pass-A column blocks of a particle scheduled together */
-    int32_t pad;
+    int32_t radix_bits_a;       /* pass-A full-stage radix: 4 (radix 16) or 3 (radix 8, twice the threads) */
     double tuned_ms_per_particle; /* time per particle of the tuned shape (0: not tuned) */
 } fcas_info;
 

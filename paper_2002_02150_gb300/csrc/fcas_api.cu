@@ -180,12 +180,12 @@ int ensure_scratch(fcas_ctx* c) {
 
 // Choose the N = N1 N2 split (bias), the pass-A column-block width (k1b; 0 = the default) and the
 // CTA grouping (sub), and lay the spectrum out for them.
-int apply_layout(fcas_ctx* c, int bias, int k1b, int sub, cudaStream_t st) {
+int apply_layout(fcas_ctx* c, int bias, int k1b, int sub, int radix_bits_a, cudaStream_t st) {
     const int log_n = c->log_n;
     const int l2 = split_log_n2_with(log_n, bias);
     const int l1 = log_n - l2;
     if (l1 > kMaxLogPass) return fail(FCAS_ERR_INVALID, "split bias %d gives a %d-point pass", bias, 1 << l1);
-    int ks[3];
+    int ks[4];
     const int nk = pass_a_k1b_variants(l2, c->setup.precision, ks);
     if (nk <= 0) return fail(FCAS_ERR_INVALID, "no pass-A shape for 2^%d-point columns", l2);
     if (k1b == 0) k1b = ks[0];
@@ -193,6 +193,8 @@ int apply_layout(fcas_ctx* c, int bias, int k1b, int sub, cudaStream_t st) {
     for (int q = 0; q < nk; ++q) ok |= ks[q] == k1b;
     if (!ok) return fail(FCAS_ERR_INVALID, "pass-A width %d not compiled for 2^%d-point columns", k1b, l2);
     if (sub < 1 || (sub & (sub - 1))) return fail(FCAS_ERR_INVALID, "CTA grouping %d is not a power of two", sub);
+    if (radix_bits_a != 4 && !(radix_bits_a == 3 && pass_a_radix8_available(l2, c->setup.precision, k1b)))
+        return fail(FCAS_ERR_INVALID, "pass-A radix %d not compiled for this shape", 1 << radix_bits_a);
     const int64_t nb = pass_b_blocks_per_particle(l1, l2, c->setup.precision);
     if (c->nb_cap && nb > c->nb_cap) return fail(FCAS_ERR_INVALID, "split bias %d needs more argmax partials", bias);
     c->split_bias = bias;
@@ -202,9 +204,10 @@ int apply_layout(fcas_ctx* c, int bias, int k1b, int sub, cudaStream_t st) {
     c->n2 = (int64_t)1 << l2;
     c->k1b = k1b;
     c->sub = sub;
+    c->radix_bits_a = radix_bits_a;
     c->nb_partials = nb;
-    cudaError_t e = launch_stage_tables(l2, c->d_stw_a64, c->d_stw_a32, st);
-    if (e == cudaSuccess) e = launch_stage_tables(l1, c->d_stw_b64, c->d_stw_b32, st);
+    cudaError_t e = launch_stage_tables(l2, radix_bits_a, c->d_stw_a64, c->d_stw_a32, st);
+    if (e == cudaSuccess) e = launch_stage_tables(l1, 4, c->d_stw_b64, c->d_stw_b32, st);
     if (e == cudaSuccess)
         e = launch_layout(c->d_ynat, c->setup.n_det, log_n, l1, l2, k1b, c->k_lo, c->k_hi, c->setup.fs, c->setup.f_low,
                           c->setup.precision, c->d_y, c->d_basis, st);
@@ -386,7 +389,7 @@ int fcas_create(fcas_ctx** out, const fcas_setup* setup, const fcas_detector* de
     FCAS_TRY(dev_alloc(&c->d_stw_a32, sizeof(float2) << kMaxLogPass, "stage twiddles"));
     FCAS_TRY(dev_alloc(&c->d_stw_b64, sizeof(double2) << kMaxLogPass, "stage twiddles"));
     FCAS_TRY(dev_alloc(&c->d_stw_b32, sizeof(float2) << kMaxLogPass, "stage twiddles"));
-    FCAS_TRY(apply_layout(c, FCAS_SPLIT_BIAS, 0, FCAS_PASS_A_SUB, st));
+    FCAS_TRY(apply_layout(c, FCAS_SPLIT_BIAS, 0, FCAS_PASS_A_SUB, 4, st));
 
     // scratch for the fitness path (partials sized for every split the tuner may choose)
     const size_t per_particle = inter_bytes_per_particle(s.precision, n);
@@ -593,18 +596,18 @@ int fcas_autotune(fcas_ctx* c, int64_t n_particles, const char* cache_path, void
     for (char& ch : gpu)
         if (ch == ' ') ch = '_';
     char key[512];
-    snprintf(key, sizeof(key), "fcas-tune-v1 %s %lld %d %d %lld", gpu.c_str(), (long long)c->setup.n_fft,
+    snprintf(key, sizeof(key), "fcas-tune-v2 %s %lld %d %d %lld", gpu.c_str(), (long long)c->setup.n_fft,
              c->setup.n_det, c->setup.precision, (long long)n_particles);
     if (cache_path) {
         if (FILE* f = fopen(cache_path, "r")) {
             char line[1024];
             while (fgets(line, sizeof(line), f)) {
                 if (strncmp(line, key, strlen(key)) != 0 || line[strlen(key)] != ' ') continue;
-                int bias, k1b, sub;
+                int bias, k1b, sub, rbits;
                 double ms;
-                if (sscanf(line + strlen(key), "%d %d %d %lf", &bias, &k1b, &sub, &ms) == 4) {
+                if (sscanf(line + strlen(key), "%d %d %d %d %lf", &bias, &k1b, &sub, &rbits, &ms) == 5) {
                     fclose(f);
-                    int rc = apply_layout(c, bias, k1b, sub, st);
+                    int rc = apply_layout(c, bias, k1b, sub, rbits, st);
                     if (rc) return rc;
                     c->tuned_ms = ms;
                     FCAS_CUDA(cudaStreamSynchronize(st));
@@ -634,18 +637,23 @@ int fcas_autotune(fcas_ctx* c, int64_t n_particles, const char* cache_path, void
     const bool prof = c->prof;
     c->prof = false;
     double best_ms = 1e300;
-    int best_bias = c->split_bias, best_k = c->k1b, best_sub = c->sub;
+    int best_bias = c->split_bias, best_k = c->k1b, best_sub = c->sub, best_rb = c->radix_bits_a;
     int last_l2 = -1;
     const int subs[4] = {1, 4, 8, 16};
     for (int bias = 0; bias <= 1 && rc == FCAS_OK; ++bias) {
         const int l2 = split_log_n2_with(c->log_n, bias);
         if (l2 == last_l2 || c->log_n - l2 > kMaxLogPass) continue;
         last_l2 = l2;
-        int ks[3];
-        const int nk = pass_a_k1b_variants(l2, c->setup.precision, ks);
+        int ks[3], rbs[4];
+        int nk = pass_a_k1b_variants(l2, c->setup.precision, ks);
+        for (int q = 0; q < nk; ++q) rbs[q] = 4;
+        if (pass_a_radix8_available(l2, c->setup.precision, 4)) {
+            ks[nk] = 4;
+            rbs[nk++] = 3;
+        }
         for (int q = 0; q < nk && rc == FCAS_OK; ++q) {
             for (int si = 0; si < 4 && rc == FCAS_OK; ++si) {
-                rc = apply_layout(c, bias, ks[q], subs[si], st);
+                rc = apply_layout(c, bias, ks[q], subs[si], rbs[q], st);
                 if (rc) break;
                 cudaError_t e = launch_passes(c, n_particles, c->d_fit, c->d_tc, st);   // warm-up
                 if (e == cudaSuccess) e = cudaEventRecord(e0, st);
@@ -664,6 +672,7 @@ int fcas_autotune(fcas_ctx* c, int64_t n_particles, const char* cache_path, void
                     best_bias = bias;
                     best_k = ks[q];
                     best_sub = subs[si];
+                    best_rb = rbs[q];
                 }
             }
         }
@@ -672,25 +681,25 @@ int fcas_autotune(fcas_ctx* c, int64_t n_particles, const char* cache_path, void
     cudaEventDestroy(e1);
     c->prof = prof;
     if (rc) return rc;
-    rc = apply_layout(c, best_bias, best_k, best_sub, st);
+    rc = apply_layout(c, best_bias, best_k, best_sub, best_rb, st);
     if (rc) return rc;
     c->tuned_ms = best_ms;
     FCAS_CUDA(cudaStreamSynchronize(st));
     if (cache_path) {
         if (FILE* f = fopen(cache_path, "a")) {
-            fprintf(f, "%s %d %d %d %.9g\n", key, best_bias, best_k, best_sub, best_ms);
+            fprintf(f, "%s %d %d %d %d %.9g\n", key, best_bias, best_k, best_sub, best_rb, best_ms);
             fclose(f);
         }
     }
     return FCAS_OK;
 }
 
-int fcas_set_shape(fcas_ctx* c, int32_t split_bias, int32_t k1b, int32_t sub, void* stream) {
+int fcas_set_shape(fcas_ctx* c, int32_t split_bias, int32_t k1b, int32_t sub, int32_t radix_bits_a, void* stream) {
     g_last_error.clear();
     if (!c) return fail(FCAS_ERR_INVALID, "fcas_set_shape: NULL context");
     if (split_bias < 0 || split_bias > 1) return fail(FCAS_ERR_INVALID, "fcas_set_shape: split_bias must be 0 or 1");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    int rc = apply_layout(c, split_bias, k1b, sub, st);
+    int rc = apply_layout(c, split_bias, k1b, sub, radix_bits_a == 0 ? 4 : radix_bits_a, st);
     if (rc) return rc;
     c->tuned_ms = 0.0;
     FCAS_CUDA(cudaStreamSynchronize(st));
@@ -893,6 +902,7 @@ int fcas_get_info(const fcas_ctx* c, fcas_info* info) {
     info->split_bias = c->split_bias;
     info->k1b = c->k1b;
     info->sub = c->sub;
+    info->radix_bits_a = c->radix_bits_a;
     info->tuned_ms_per_particle = c->tuned_ms;
     return FCAS_OK;
 }

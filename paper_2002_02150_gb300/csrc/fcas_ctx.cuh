@@ -34,6 +34,7 @@ struct fcas_ctx {
     double2* d_ynat = nullptr;      // whitened band spectrum in natural order [D][N/2] (binary64)
     int split_bias = 0;             // N2 = 2^(floor(log2 N / 2) - split_bias)
     int k1b = 0;                    // pass-A columns per CTA (layout of d_y and d_basis)
+    int radix_bits_a = 4;           // pass-A full-stage radix bits (4: radix 16, 3: radix 8)
     int sub = 8;                    // pass-A column blocks scheduled together
     double tuned_ms = 0.0;          // per-particle time of the tuned configuration (0: not tuned)
     int64_t nb_cap = 0;             // argmax partials per particle the scratch holds
@@ -92,6 +93,7 @@ inline FitnessPlan make_plan(const fcas_ctx* c) {
     p.stw_a = fp32 ? (const void*)c->d_stw_a32 : (const void*)c->d_stw_a64;
     p.stw_b = fp32 ? (const void*)c->d_stw_b32 : (const void*)c->d_stw_b64;
     p.k1b = c->k1b;
+    p.radix_bits_a = c->radix_bits_a;
     p.sub = c->sub;
     p.tw_lo = c->d_twlo;
     p.tw_hi = c->d_twhi;

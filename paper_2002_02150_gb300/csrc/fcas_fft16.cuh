@@ -3,7 +3,9 @@
 // A transform of length L = 2^LOG_L (L >= 16) is held by G = L / 16 threads, thread j owning the
 // 16 values at positions j + q G (q = 0..15) on entry and on exit (natural order). Stage s has
 // radix R_s = 16 while at least four bits of L remain, then one stage takes the remaining 1-3
-// bits; for L < 16 a single stage of radix L is used (V = L values per thread, G = 1). Each stage
+// bits; for L < 16 a single stage of radix L is used (V = L values per thread, G = 1). The same
+// code with radix-8 full stages (8 values per thread, twice the threads) trades one more
+// shared-memory exchange for half the registers. Each stage
 // is the Stockham self-sorting step: task jj reads x[jj + r L/R], multiplies by
 // e^{S 2 pi i r (jj mod Ns) / (Ns R)}, applies the R-point DFT in registers and writes to
 // (jj / Ns) Ns R + (jj mod Ns) + r Ns. Consecutive stages exchange data through shared memory,
@@ -17,10 +19,13 @@
 
 namespace fcas {
 
-__host__ __device__ constexpr int fft16_radix_bits(int log_l, int done) {
-    return (log_l - done) >= 4 ? 4 : (log_l - done);
+// MAXRB: radix bits of the full stages (4: radix 16, 16 values per thread; 3: radix 8, 8 values)
+__host__ __device__ constexpr int fftr_radix_bits(int log_l, int done, int maxrb) {
+    return (log_l - done) >= maxrb ? maxrb : (log_l - done);
 }
-__host__ __device__ constexpr int fft16_v(int log_l) { return log_l >= 4 ? 16 : (1 << log_l); }
+__host__ __device__ constexpr int fftr_v(int log_l, int maxrb) { return log_l >= maxrb ? (1 << maxrb) : (1 << log_l); }
+__host__ __device__ constexpr int fft16_radix_bits(int log_l, int done) { return fftr_radix_bits(log_l, done, 4); }
+__host__ __device__ constexpr int fft16_v(int log_l) { return fftr_v(log_l, 4); }
 __host__ __device__ constexpr int fft16_pad(int e) { return e + (e >> 4); }
 __host__ __device__ constexpr int fft16_buf_elems(int log_l) { return fft16_pad(1 << log_l); }
 
@@ -133,14 +138,14 @@ __device__ __forceinline__ void dft_r(C (&a)[R]) {
     }
 }
 
-template <typename Real, int S, int LOG_L, int DONE>
-__device__ __forceinline__ void fft16_stage(cplx<Real> (&v)[fft16_v(LOG_L)], cplx<Real>* buf, int es, int j,
-                                            const cplx<Real>* __restrict__ stw) {
+template <typename Real, int S, int LOG_L, int DONE, int MAXRB>
+__device__ __forceinline__ void fftr_stage(cplx<Real> (&v)[fftr_v(LOG_L, MAXRB)], cplx<Real>* buf, int es, int j,
+                                           const cplx<Real>* __restrict__ stw) {
     using C = cplx<Real>;
     constexpr int L = 1 << LOG_L;
-    constexpr int V = fft16_v(LOG_L);
+    constexpr int V = fftr_v(LOG_L, MAXRB);
     constexpr int G = L / V;
-    constexpr int RB = fft16_radix_bits(LOG_L, DONE);
+    constexpr int RB = fftr_radix_bits(LOG_L, DONE, MAXRB);
     constexpr int R = 1 << RB;
     constexpr int T = V / R;
     constexpr int NS = 1 << DONE;
@@ -207,12 +212,13 @@ __device__ __forceinline__ void fft16_stage(cplx<Real> (&v)[fft16_v(LOG_L)], cpl
         for (int h = 0; h < T; ++h) {
             const int jj = j + h * G;
             const int dst = (jj / NS) * NS * R + (jj & (NS - 1));
-            if constexpr ((NS == 1 && R == 16) || NS % 16 == 0) {
-                // pad(dst + r NS) = pad(dst) + r (NS + NS/16), or + r when NS = 1 and R = 16
-                constexpr int STRIDE = NS == 1 ? 1 : NS + NS / 16;
+            // pad(dst + r NS) = pad(dst) + r NS + (r NS >> 4) when adding r NS to dst never carries into
+            // a new group of 16 differently from r NS itself: NS a multiple of 16, or NS dividing 16
+            // with NS R a multiple of 16 (dst mod 16 < NS), or NS = 1 with R = 8 (dst mod 16 in {0, 8})
+            if constexpr (NS % 16 == 0 || (16 % NS == 0 && (NS * R) % 16 == 0) || (NS == 1 && R == 8)) {
                 C* wb = buf + fft16_pad(dst) * es;
 #pragma unroll
-                for (int r = 0; r < R; ++r) wb[r * STRIDE * es] = v[h + r * T];
+                for (int r = 0; r < R; ++r) wb[(r * NS + ((r * NS) >> 4)) * es] = v[h + r * T];
             } else {
 #pragma unroll
                 for (int r = 0; r < R; ++r) buf[fft16_pad(dst + r * NS) * es] = v[h + r * T];
@@ -222,13 +228,19 @@ __device__ __forceinline__ void fft16_stage(cplx<Real> (&v)[fft16_v(LOG_L)], cpl
     }
 }
 
-template <typename Real, int S, int LOG_L, int DONE = 0>
+template <typename Real, int S, int LOG_L, int MAXRB, int DONE = 0>
+__device__ __forceinline__ void fftr(cplx<Real> (&v)[fftr_v(LOG_L, MAXRB)], cplx<Real>* buf, int es, int j,
+                                     const cplx<Real>* __restrict__ stw) {
+    if constexpr (DONE < LOG_L) {
+        fftr_stage<Real, S, LOG_L, DONE, MAXRB>(v, buf, es, j, stw);
+        fftr<Real, S, LOG_L, MAXRB, DONE + fftr_radix_bits(LOG_L, DONE, MAXRB)>(v, buf, es, j, stw);
+    }
+}
+
+template <typename Real, int S, int LOG_L>
 __device__ __forceinline__ void fft16(cplx<Real> (&v)[fft16_v(LOG_L)], cplx<Real>* buf, int es, int j,
                                       const cplx<Real>* __restrict__ stw) {
-    if constexpr (DONE < LOG_L) {
-        fft16_stage<Real, S, LOG_L, DONE>(v, buf, es, j, stw);
-        fft16<Real, S, LOG_L, DONE + fft16_radix_bits(LOG_L, DONE)>(v, buf, es, j, stw);
-    }
+    fftr<Real, S, LOG_L, 4>(v, buf, es, j, stw);
 }
 
 }  // namespace fcas

@@ -182,15 +182,15 @@ struct DetConst {
     Real dh[FCAS_MAX_DET], dl[FCAS_MAX_DET], w1[FCAS_MAX_DET], w2[FCAS_MAX_DET];
 };
 
-template <typename Real, int LOG_L, int K1B>
-__global__ void __launch_bounds__(K1B * ((1 << LOG_L) / shape_v(LOG_L)), 1)
+template <typename Real, int LOG_L, int K1B, int MAXRB>
+__global__ void __launch_bounds__(K1B * ((1 << LOG_L) / fftr_v(LOG_L, MAXRB)), 1)
 pass_a_kernel(const cplx<Real>* __restrict__ y, const Basis<Real>* __restrict__ basis,
               const ParticleParams* __restrict__ params, int64_t p0, int64_t np, int n_det, int log_n1, int sub_req,
               cplx<Real>* __restrict__ out, const cplx<Real>* __restrict__ stw,
               const cplx<Real>* __restrict__ tw_lo, const cplx<Real>* __restrict__ tw_hi) {
     using C = cplx<Real>;
     constexpr int L = 1 << LOG_L;
-    constexpr int V = shape_v(LOG_L);
+    constexpr int V = fftr_v(LOG_L, MAXRB);
     constexpr int G = L / V;
     constexpr int VH = V / 2;    // values with k2 < L/2; the rest of the column is zero (k >= N/2)
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -300,7 +300,7 @@ pass_a_kernel(const cplx<Real>* __restrict__ y, const Basis<Real>* __restrict__ 
         for (int q = 0; q < VH; ++q) v[q] = a == 0 ? r1[q] : r2[q];
 #pragma unroll
         for (int q = VH; q < V; ++q) v[q] = mkc((Real)0, (Real)0);
-        fft16<Real, +1, LOG_L>(v, smem + c, K1B, j, stw);
+        fftr<Real, +1, LOG_L, MAXRB>(v, smem + c, K1B, j, stw);
         C* orow = out + ((p * kSeries + a) * L) * (int64_t)n1 + k1;
         // e^{2 pi i k1 ta / N} for ta = j + q G: the value at q = 0 times powers of the step e^{2 pi i k1 G / N}
         const int m0 = k1 * j, ms = k1 * G;   // < N
@@ -467,12 +467,12 @@ int pass_b_blocks_per_particle(int log_n1, int log_n2, int precision) {
     }
 }
 
-template <typename Real, int LG, int K1B>
+template <typename Real, int LG, int K1B, int MAXRB = 4>
 static cudaError_t pass_a_at(const FitnessPlan& pl, const ParticleParams* params, int64_t p0, int64_t np, void* inter,
                              cudaStream_t s) {
-    constexpr int THREADS = K1B * ((1 << LG) / shape_v(LG));
+    constexpr int THREADS = K1B * ((1 << LG) / fftr_v(LG, MAXRB));
     const size_t smem = sizeof(cplx<Real>) * (size_t)K1B * fft16_buf_elems(LG);
-    auto kern = pass_a_kernel<Real, LG, K1B>;
+    auto kern = pass_a_kernel<Real, LG, K1B, MAXRB>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t ctas = np * ((1 << pl.log_n1) / K1B);
@@ -496,6 +496,12 @@ static cudaError_t pass_a_lg(const FitnessPlan& pl, const ParticleParams* params
                              void* inter, cudaStream_t s) {
     constexpr int RB = sizeof(Real);
     constexpr int KD = pass_a_k1b(LG, RB);
+    if (pl.radix_bits_a == 3) {
+        // radix-8 stages: 8 values per thread, 1024-thread CTAs of 4 columns (FP32, >= 2^10 points)
+        if constexpr (RB == 4 && LG >= 10 && LG <= 12)
+            if (pl.k1b == 4) return pass_a_at<Real, LG, 4, 3>(pl, params, p0, np, inter, s);
+        return cudaErrorInvalidValue;
+    }
     if (pl.k1b == KD) return pass_a_at<Real, LG, KD>(pl, params, p0, np, inter, s);
     if constexpr (RB == 4 && LG >= 8) {
         if constexpr (k1b_variant_ok<LG, RB>(KD / 2))
@@ -504,6 +510,10 @@ static cudaError_t pass_a_lg(const FitnessPlan& pl, const ParticleParams* params
             if (pl.k1b == KD * 2) return pass_a_at<Real, LG, (KD * 2 <= 16 ? KD * 2 : 16)>(pl, params, p0, np, inter, s);
     }
     return cudaErrorInvalidValue;
+}
+
+bool pass_a_radix8_available(int log_n2, int precision, int k1b) {
+    return precision == FCAS_PREC_FP32 && log_n2 >= 10 && log_n2 <= 12 && k1b == 4;
 }
 
 int pass_a_k1b_variants(int log_n2, int precision, int* out) {
@@ -575,15 +585,15 @@ template cudaError_t launch_pass_b<double>(const FitnessPlan&, const ParticlePar
 // ------------------------------------------------------------------------------------------
 // per-stage twiddle tables of the radix-16 transforms (create time)
 // ------------------------------------------------------------------------------------------
-__global__ void stage_table_kernel(int log_l, double2* t64, float2* t32) {
+__global__ void stage_table_kernel(int log_l, int maxrb, double2* t64, float2* t32) {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     const int l = 1 << log_l;
     if (m >= l) return;
     double2 val = make_double2(1.0, 0.0);
     // find the stage that owns entry m: (Ns - 1) <= m < Ns R - 1
-    for (int done = 0; done < log_l; done += fft16_radix_bits(log_l, done)) {
+    for (int done = 0; done < log_l; done += fftr_radix_bits(log_l, done, maxrb)) {
         const int ns = 1 << done;
-        const int r_ = 1 << fft16_radix_bits(log_l, done);
+        const int r_ = 1 << fftr_radix_bits(log_l, done, maxrb);
         if (ns > 1 && m >= ns - 1 && m < ns * r_ - 1) {
             const int off = m - (ns - 1);
             const int r = off / ns + 1;
@@ -599,9 +609,9 @@ __global__ void stage_table_kernel(int log_l, double2* t64, float2* t32) {
     t32[m] = make_float2((float)val.x, (float)val.y);
 }
 
-cudaError_t launch_stage_tables(int log_l, double2* t64, float2* t32, cudaStream_t s) {
+cudaError_t launch_stage_tables(int log_l, int maxrb, double2* t64, float2* t32, cudaStream_t s) {
     const int l = 1 << log_l;
-    stage_table_kernel<<<(l + 255) / 256, 256, 0, s>>>(log_l, t64, t32);
+    stage_table_kernel<<<(l + 255) / 256, 256, 0, s>>>(log_l, maxrb, t64, t32);
     return cudaGetLastError();
 }
 

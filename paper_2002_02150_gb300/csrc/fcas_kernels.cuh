@@ -34,6 +34,7 @@ struct FitnessPlan {
     const void* stw_a;            // per-stage twiddles of the length-N2 transforms
     const void* stw_b;            // per-stage twiddles of the length-N1 transforms
     int k1b;                      // columns per pass-A CTA (must match the layout of y and basis)
+    int radix_bits_a;             // pass-A full-stage radix bits (4: radix 16, 3: radix 8; matches stw_a)
     int sub;                      // adjacent column blocks of a particle scheduled together
     const void* tw_lo;            // e^{2 pi i m / N}, m < 4096
     const void* tw_hi;            // e^{2 pi i 4096 m / N}, m < max(1, N / 4096)
@@ -60,7 +61,9 @@ int pass_b_blocks_per_particle(int log_n1, int log_n2, int precision);
 int pass_a_k1b_for(int log_n2, int precision);
 // compiled pass-A column-block widths for a length: writes up to 3 values, returns the count
 int pass_a_k1b_variants(int log_n2, int precision, int* out);
-cudaError_t launch_stage_tables(int log_l, double2* t64, float2* t32, cudaStream_t s);
+cudaError_t launch_stage_tables(int log_l, int maxrb, double2* t64, float2* t32, cudaStream_t s);
+// pass A with radix-8 stages (8 values per thread) is compiled for these shapes
+bool pass_a_radix8_available(int log_n2, int precision, int k1b);
 
 // ---- adjoint (fcas_grad.cu) ----
 template <typename Real>

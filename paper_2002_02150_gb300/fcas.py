@@ -42,7 +42,7 @@ class fcas_info(ctypes.Structure):
                 ("chunk", ctypes.c_int64), ("n_det", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("scale", ctypes.c_double), ("sigma2", ctypes.c_double * FCAS_MAX_DET),
                 ("inter_bytes", ctypes.c_int64), ("series", ctypes.c_int64), ("split_bias", ctypes.c_int32),
-                ("k1b", ctypes.c_int32), ("sub", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("k1b", ctypes.c_int32), ("sub", ctypes.c_int32), ("radix_bits_a", ctypes.c_int32),
                 ("tuned_ms_per_particle", ctypes.c_double)]
 
 
@@ -106,7 +106,7 @@ def load_library():
     lib.fcas_gradient.restype = i32
     lib.fcas_autotune.argtypes = [vp, i64, ctypes.c_char_p, vp]
     lib.fcas_autotune.restype = i32
-    lib.fcas_set_shape.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, vp]
+    lib.fcas_set_shape.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, vp]
     lib.fcas_set_shape.restype = i32
     lib.fcas_group_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int32, ctypes.POINTER(vp), ctypes.c_int32]
     lib.fcas_group_create.restype = i32
@@ -392,9 +392,9 @@ def fcas_autotune(ctx, n_particles=64, cache_path=None, stream=None):
     return fcas_get_info(ctx)
 
 
-def fcas_set_shape(ctx, split_bias=0, k1b=0, sub=8, stream=None):
+def fcas_set_shape(ctx, split_bias=0, k1b=0, sub=8, radix_bits_a=4, stream=None):
     s = ctypes.c_void_p(int(stream)) if stream is not None else ctypes.c_void_p(0)
-    _check(load_library().fcas_set_shape(ctx.handle, int(split_bias), int(k1b), int(sub), s))
+    _check(load_library().fcas_set_shape(ctx.handle, int(split_bias), int(k1b), int(sub), int(radix_bits_a), s))
     return fcas_get_info(ctx)
 
 

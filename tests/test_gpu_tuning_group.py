@@ -27,12 +27,13 @@ def _shapes(ctx):
     out = []
     for bias in (0, 1):
         for k in (1, 2, 4, 8, 16):
-            try:
-                fc.fcas_set_shape(ctx, bias, k, 8)
-            except fc.FcasError:
-                continue
-            for sub in (1, 8):
-                out.append((bias, k, sub))
+            for rb in (4, 3):
+                try:
+                    fc.fcas_set_shape(ctx, bias, k, 8, rb)
+                except fc.FcasError:
+                    continue
+                for sub in (1, 8):
+                    out.append((bias, k, sub, rb))
     return out
 
 
@@ -45,12 +46,12 @@ def test_every_compiled_shape_matches_the_oracle(w):
     with make_ctx(w, data, "fp32") as ctx:
         shapes = _shapes(ctx)
         assert len(shapes) >= 4
-        for bias, k, sub in shapes:
-            info = fc.fcas_set_shape(ctx, bias, k, sub)
-            assert (info["split_bias"], info["k1b"], info["sub"]) == (bias, k, sub)
+        for bias, k, sub, rb in shapes:
+            info = fc.fcas_set_shape(ctx, bias, k, sub, rb)
+            assert (info["split_bias"], info["k1b"], info["sub"], info["radix_bits_a"]) == (bias, k, sub, rb)
             assert info["n1"] * info["n2"] == w.n_fft
             f, t = gpu_fitness(ctx, theta)
-            assert_parity(setup, theta, f, t, "fp32", f"shape {bias, k, sub}")
+            assert_parity(setup, theta, f, t, "fp32", f"shape {bias, k, sub, rb}")
 
 
 def test_shapes_of_the_60min_transform_agree():
@@ -60,8 +61,10 @@ def test_shapes_of_the_60min_transform_agree():
     theta = sd.make_particles(w, 6, seed=2)
     with make_ctx(w, data, "fp32", max_batch=8) as ctx:
         ref_f, ref_t = gpu_fitness(ctx, theta)
-        for bias, k, sub in _shapes(ctx):
-            fc.fcas_set_shape(ctx, bias, k, sub)
+        shapes = _shapes(ctx)
+        assert any(rb == 3 for *_, rb in shapes)
+        for bias, k, sub, rb in shapes:
+            fc.fcas_set_shape(ctx, bias, k, sub, rb)
             f, t = gpu_fitness(ctx, theta)
             np.testing.assert_allclose(f, ref_f, rtol=2e-5)
             np.testing.assert_array_equal(t, ref_t)
@@ -82,7 +85,7 @@ def test_autotune_applies_the_fastest_shape_and_caches_it(tmp_path):
     assert len(lines) == 1
     with make_ctx(w, data, "fp32") as ctx2:
         info2 = fc.fcas_autotune(ctx2, 64, cache)
-        for key in ("split_bias", "k1b", "sub"):
+        for key in ("split_bias", "k1b", "sub", "radix_bits_a"):
             assert info2[key] == info[key]
     assert len(open(cache).read().splitlines()) == 1      # a hit adds nothing
 
