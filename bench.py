@@ -13,7 +13,6 @@ its own data realisation and particle batch, no data-path collective).
 
 import argparse
 import dataclasses
-import glob
 import hashlib
 import json
 import os
@@ -143,10 +142,16 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------------------- roofline
+FITNESS_KERNEL_SOURCES = ["paper_2002_02150_gb300/csrc/fcas_kernels.cu", "paper_2002_02150_gb300/csrc/fcas_kernels.cuh",
+                          "paper_2002_02150_gb300/csrc/fcas_fft16.cuh", "paper_2002_02150_gb300/csrc/fcas_internal.cuh",
+                          "include/fcas.h"]
+
+
 def kernel_source_hash():
+    """Hash of the files the fitness kernels (pass A, pass B) are compiled from."""
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2002_02150_gb300", "csrc", "*"))):
-        h.update(open(p, "rb").read())
+    for p in FITNESS_KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, p), "rb").read())
     return h.hexdigest()[:16]
 
 

@@ -196,6 +196,13 @@ int fcas_pso_update(const fcas_pso_config* cfg, int32_t iter, const double* fitn
                     const fcas_pso_state* state, void* stream);
 
 /*
+ * Parameters (alpha, delta, tau0, tau1.5) of normalised positions x [rows][4] (device), written to
+ * theta [rows][4] (device); NaN for a particle outside the box (fcas_fitness then skips it).
+ * Asynchronous.
+ */
+int fcas_pso_theta(const fcas_pso_config* cfg, const double* x, double* theta, void* stream);
+
+/*
  * fcas_search -- the full search on the context's data: n_runs x n_particles particles evolve
  * together on the device for n_iter iterations; every iteration (positions -> parameters,
  * fitness, update) is one CUDA-graph launch with no host round trip. results: host array

@@ -339,8 +339,8 @@ int fcas_create(fcas_ctx** out, const fcas_setup* setup, const fcas_detector* de
     FCAS_TRYCUDA(cudaMemcpyAsync(c->d_det, det, sizeof(double) * 9 * D, cudaMemcpyHostToDevice, st));
 
     // template norms and the power-of-two scale that brings them near 1
-    FCAS_TRY(dev_alloc(&d_sig, sizeof(double) * D, "sigma2"));
-    FCAS_TRYCUDA(launch_sigma2(d_psd, D, psd_row, k_lo, k_hi, c->df, d_sig, st));
+    FCAS_TRY(dev_alloc(&d_sig, sizeof(double) * D * 257, "sigma2"));
+    FCAS_TRYCUDA(launch_sigma2(d_psd, D, psd_row, k_lo, k_hi, c->df, d_sig, d_sig + D, st));
     FCAS_TRYCUDA(cudaMemcpyAsync(c->sigma2, d_sig, sizeof(double) * D, cudaMemcpyDeviceToHost, st));
     FCAS_TRYCUDA(cudaStreamSynchronize(st));
     double smax = 0.0;

@@ -81,14 +81,19 @@ cudaError_t launch_check_psd(const double* psd, int n_det, int64_t row, int64_t 
 }
 
 // ------------------------------------------------------------------------------------------
-// <h_c|h_c>^i = 4 df sum_{k in band} f_k^{-7/3} / S^i[k] (Sec. II.D), fixed-order block reduction
+// <h_c|h_c>^i = 4 df sum_{k in band} f_k^{-7/3} / S^i[k] (Sec. II.D), fixed-order two-level reduction
 // ------------------------------------------------------------------------------------------
-__global__ void sigma2_kernel(const double* __restrict__ psd, int64_t row, int64_t k_lo, int64_t k_hi, double df,
-                              double* __restrict__ sigma2) {
+constexpr int kSigmaBlocks = 256;
+
+// stage 1: block b of detector i sums the band bins k = k_lo + b, k_lo + b + kSigmaBlocks, ... in a
+// fixed tree order; stage 2 adds the kSigmaBlocks partials of each detector in order.
+__global__ void sigma2_partial_kernel(const double* __restrict__ psd, int64_t row, int64_t k_lo, int64_t k_hi,
+                                      double df, double* __restrict__ partial) {
     __shared__ double acc[256];
-    const int i = blockIdx.x;
+    const int i = blockIdx.y;
     double a = 0.0;
-    for (int64_t k = k_lo + threadIdx.x; k <= k_hi; k += blockDim.x) {
+    for (int64_t k = k_lo + blockIdx.x + (int64_t)kSigmaBlocks * threadIdx.x; k <= k_hi;
+         k += (int64_t)kSigmaBlocks * blockDim.x) {
         const double f = (double)k * df;
         a += pow(f, -7.0 / 3.0) / psd[i * row + k];
     }
@@ -98,12 +103,24 @@ __global__ void sigma2_kernel(const double* __restrict__ psd, int64_t row, int64
         if ((int)threadIdx.x < w) acc[threadIdx.x] += acc[threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x == 0) sigma2[i] = 4.0 * df * acc[0];
+    if (threadIdx.x == 0) partial[i * kSigmaBlocks + blockIdx.x] = acc[0];
 }
 
+__global__ void sigma2_final_kernel(const double* __restrict__ partial, double df, double* __restrict__ sigma2) {
+    const int i = blockIdx.x;
+    if (threadIdx.x != 0) return;
+    double a = 0.0;
+    for (int b = 0; b < kSigmaBlocks; ++b) a += partial[i * kSigmaBlocks + b];
+    sigma2[i] = 4.0 * df * a;
+}
+
+// <h_c|h_c>^i = 4 df sum_{k in band} f_k^{-7/3} / S^i[k] (Sec. II.D); `work` holds n_det * 256 doubles
 cudaError_t launch_sigma2(const double* psd, int n_det, int64_t row, int64_t k_lo, int64_t k_hi, double df,
-                          double* sigma2, cudaStream_t s) {
-    sigma2_kernel<<<n_det, 256, 0, s>>>(psd, row, k_lo, k_hi, df, sigma2);
+                          double* sigma2, double* work, cudaStream_t s) {
+    sigma2_partial_kernel<<<dim3(kSigmaBlocks, n_det), 256, 0, s>>>(psd, row, k_lo, k_hi, df, work);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    sigma2_final_kernel<<<n_det, 32, 0, s>>>(work, df, sigma2);
     return cudaGetLastError();
 }
 

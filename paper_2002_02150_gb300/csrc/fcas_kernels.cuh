@@ -80,7 +80,7 @@ cudaError_t launch_check_finite(const double* x, int64_t n, int* flag, cudaStrea
 cudaError_t launch_check_psd(const double* psd, int n_det, int64_t row, int64_t k_lo, int64_t k_hi, int* flag,
                              cudaStream_t s);
 cudaError_t launch_sigma2(const double* psd, int n_det, int64_t row, int64_t k_lo, int64_t k_hi, double df,
-                          double* sigma2, cudaStream_t s);
+                          double* sigma2, double* work, cudaStream_t s);
 cudaError_t launch_data_fft(const double* data, int n_det, int64_t n_samples, int log_n, int log_n1, int log_n2,
                             const double2* tw64, int tw_shift_a, int tw_shift_b, const double2* twlo64,
                             const double2* twhi64, double2* work, double2* spec, cudaStream_t s);

@@ -259,3 +259,13 @@ extern "C" int fcas_pso_update(const fcas_pso_config* cfg, int32_t iter, const d
     cudaError_t e = launch_pso_update(pso_dev(cfg), iter, fitness, tc, s, static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? FCAS_OK : report_error(FCAS_ERR_CUDA, cudaGetErrorString(e));
 }
+
+extern "C" int fcas_pso_theta(const fcas_pso_config* cfg, const double* x, double* theta, void* stream) {
+    char msg[256];
+    int rc = pso_validate(cfg, msg, sizeof(msg));
+    if (rc) return report_error(rc, msg);
+    if (!x || !theta) return report_error(FCAS_ERR_INVALID, "fcas_pso_theta: NULL array");
+    PsoStateDev s{const_cast<double*>(x), nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaError_t e = launch_pso_theta(pso_dev(cfg), s, theta, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? FCAS_OK : report_error(FCAS_ERR_CUDA, cudaGetErrorString(e));
+}

@@ -100,6 +100,8 @@ def load_library():
     lib.fcas_pso_update.argtypes = [ctypes.POINTER(fcas_pso_config), ctypes.c_int32, vp, vp,
                                     ctypes.POINTER(fcas_pso_state), vp]
     lib.fcas_pso_update.restype = i32
+    lib.fcas_pso_theta.argtypes = [ctypes.POINTER(fcas_pso_config), vp, vp, vp]
+    lib.fcas_pso_theta.restype = i32
     lib.fcas_search.argtypes = [vp, ctypes.POINTER(fcas_pso_config), ctypes.POINTER(fcas_search_result), vp]
     lib.fcas_search.restype = i32
     lib.fcas_gradient.argtypes = [vp, i64, vp, vp, vp, vp]
@@ -271,6 +273,17 @@ def pso_config(n_runs=8, n_particles=40, n_iter=2000, n_neighbours=1, seed=0, bo
     cfg.box[:] = [float(b) for b in box]
     cfg.w_start, cfg.w_end, cfg.c1, cfg.c2, cfg.vmax = w_start, w_end, c1, c2, vmax
     return cfg
+
+
+def pso_theta(cfg, x, theta=None, stream=None):
+    """Parameters of normalised positions x (torch CUDA (rows, 4)) by the library's kernel; NaN outside
+    the box (not evaluated)."""
+    import torch
+    if theta is None:
+        theta = torch.empty_like(x)
+    _check(load_library().fcas_pso_theta(ctypes.byref(cfg), ctypes.c_void_p(x.data_ptr()),
+                                         ctypes.c_void_p(theta.data_ptr()), _stream(stream, x)))
+    return theta
 
 
 def _state(x, v, pbest_x, pbest_f, pbest_tc):

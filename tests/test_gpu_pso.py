@@ -111,3 +111,45 @@ def test_search_recovers_a_noiseless_injection():
     assert best["fitness"] >= 0.95 * inj["snr"] ** 2
     assert best["fitness"] <= inj["snr"] ** 2 * (1 + 1e-4)
     assert abs(best["theta"][2] / t0 - 1) < 0.01
+
+
+def test_checkpoint_and_resume_is_bit_identical():
+    """The swarm state is plain device arrays and the random numbers are counter based: copying the
+    state to the host after 3 iterations and restoring it later continues exactly like a run that
+    never stopped."""
+    import torch
+    import paper_2002_02150_gb300 as fc
+    w = sd.SMALL
+    data = sd.make_dataset(w, 2)
+    _, cfg = _cfgs(w, n_runs=2, n_particles=10, n_iter=6, seed=17)
+    rows = 20
+    dev = dict(device="cuda:0")
+
+    def fresh():
+        x = torch.empty((rows, 4), dtype=torch.float64, **dev)
+        return [x, torch.empty_like(x), torch.empty_like(x), torch.empty(rows, dtype=torch.float64, **dev),
+                torch.empty(rows, dtype=torch.int64, **dev)]
+
+    with make_ctx(w, data, "fp32") as ctx:
+        def step(state, it):
+            th = fc.pso_theta(cfg, state[0])
+            f, t = fc.fcas_fitness(ctx, th)
+            fc.fcas_pso_update(cfg, it, f, t, *state)
+
+        a = fresh()
+        fc.fcas_pso_init(cfg, *a)
+        for it in range(6):
+            step(a, it)
+        b = fresh()
+        fc.fcas_pso_init(cfg, *b)
+        for it in range(3):
+            step(b, it)
+        saved = [t.cpu().numpy().copy() for t in b]          # checkpoint
+        c = fresh()
+        for dst, src in zip(c, saved):                       # resume into new buffers
+            dst.copy_(torch.from_numpy(src))
+        for it in range(3, 6):
+            step(c, it)
+        torch.cuda.synchronize()
+    for u, v in zip(a, c):
+        assert torch.equal(u, v)
