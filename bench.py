@@ -42,10 +42,12 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=sd.C2.name)
     ap.add_argument("--fp64-steps", type=int, default=2)
-    ap.add_argument("--cpu-sample", type=int, default=4, help="particles in the oracle CPU-baseline sample")
+    ap.add_argument("--cpu-sample", type=int, default=1, help="particles per host core in the oracle CPU baseline")
     ap.add_argument("--particles", type=int, default=0, help="particles per GPU (0 = the workload's batch)")
     ap.add_argument("--max-batch", type=int, default=0, help="particles per internal chunk (0 = automatic)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
+    ap.add_argument("--cufft-batches", type=int, default=2,
+                    help="timed batches of 4 particles of the cuFFT comparison form (0 = skip)")
     ap.add_argument("--no-search", action="store_true", help="skip the PSO search measurements")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shape (no autotuning)")
     ap.add_argument("--group-segments", type=int, default=6,
@@ -269,6 +271,11 @@ def bench_ours(args, ranks):
                "d2h_bytes_per_step": int(n * 16)}
     ctx.close()
 
+    cufft = None
+    if args.cufft_batches > 0:
+        cufft = bench_cufft(w, data, theta, fit.double().cpu().numpy(), tc.cpu().numpy(), dev,
+                            steps=args.cufft_batches)
+
     # plain binary64 form on the same workload (fewer steps: it is binary64-ALU bound)
     fp64 = None
     if args.fp64_steps > 0:
@@ -303,7 +310,7 @@ def bench_ours(args, ranks):
                              "autotuned": info["tuned_ms_per_particle"] > 0},
                    "l2": "inputs larger than L2 (intermediate %.1f GB per step), no flush" % (n * info["inter_bytes"] / 1e9)},
         "roofline": roofline, "kernels": kernels, "gpu_launches": gpu_launches, "e2e": e2e, "clocks": clock,
-        "fp64_form": fp64,
+        "fp64_form": fp64, "cufft_form": cufft,
         "search_time_over_data_time": (search["search_time_over_data_time"] if search else
                                        {"value": round(PSO_EVALS / value / DATA_SECONDS, 5),
                                         "how": "extrapolated: 8 runs x 40 particles x 2000 iterations / value / 3600 s"}),
@@ -312,8 +319,115 @@ def bench_ours(args, ranks):
         "paper_context": {"search_over_data": [1.4, 0.5], "hardware": "1 KNL node per PSO run, FP64"},
     }
     if ranks.rank == 0 and args.cpu_sample > 0:
-        out["cpu_baseline"] = cpu_baseline(w, data, theta, args.cpu_sample)
+        out["cpu_baseline"] = cpu_baseline(w, ranks.rank, theta, args.cpu_sample)
     return out
+
+
+C_LIGHT = 299792458.0
+
+
+def _chirp_coefficients(tau0, tau15, f_star):
+    """Chirp-phase coefficients in turns for the powers phi^-5/3, phi^-1, phi^-2/3, phi^-1/3 of
+    phi = f / f_* (restricted 2PN phase in chirp times, Sec. II.B)."""
+    x = 5.0 * tau15 / (32.0 * np.pi * tau0)
+    eta = x ** (-2.0 / 3.0) / (8.0 * f_star * tau15)
+    tau1 = 5.0 / (192.0 * np.pi * f_star * eta * x) * (743.0 / 336.0 + 11.0 * eta / 4.0)
+    tau2 = 5.0 / (128.0 * np.pi * f_star * eta * x ** (1.0 / 3.0)) * (
+        3058673.0 / 1016064.0 + 5429.0 * eta / 1008.0 + 617.0 * eta ** 2 / 144.0)
+    return 0.6 * f_star * tau0, f_star * tau1, -1.5 * f_star * tau15, 3.0 * f_star * tau2
+
+
+def bench_cufft(w, data, theta, fit_ref, tc_ref, dev, batch=4, steps=2):
+    """The straightforward GPU form, timed for comparison: per particle and detector the spectrum
+    Q_i[k] = 4 df y~^i[k] e^{2 pi i f_k Delta^i} h~_c*[k] is formed by PyTorch element-wise kernels
+    (binary64 phase, complex64 product), transformed by cuFFT (torch.fft.ifft, complex64, length N,
+    one transform per detector), then projected, Gamma^2(t) = X_c^T G^-1 X_c + X_s^T G^-1 X_s, and
+    maximised over t, each a separate kernel (the projection through the Cholesky factor of G^-1,
+    as a sum of squares). Its results are compared with the fused path's."""
+    import torch
+    d9 = np.asarray(data["det"], dtype=np.float64)
+    n_det, n, fs = d9.shape[0], w.n_fft, w.fs
+    df = fs / n
+    kk = torch.arange(n // 2 + 1, device=dev)
+    f_all = kk.double() * df
+    kf = kk.double() * fs                                    # band f_low < f <= f_high, 0 < k < N/2
+    sel = ((kf > w.f_low * n) & (kf <= w.f_high * n) & (kk > 0) & (kk < n // 2)).nonzero().squeeze(1)
+    f = f_all[sel]
+    x = torch.zeros(n_det, n, dtype=torch.float64, device=dev)
+    x[:, : w.n_samples] = torch.as_tensor(np.asarray(data["data"]), device=dev)
+    psd = torch.as_tensor(np.asarray(data["psd"]), device=dev)[:, sel]
+    y = torch.fft.rfft(x, dim=1)[:, sel] / fs / psd
+    del x
+    sigma2 = (4.0 * df * (f ** (-7.0 / 3.0))[None, :] / psd).sum(1).cpu().numpy()
+    ybase = y * (4.0 * df * f ** (-7.0 / 6.0))[None, :] * np.exp(-0.25j * np.pi)
+    del y, psd
+    phi = f / w.f_low
+    powers = torch.stack([phi ** (-5.0 / 3.0), 1.0 / phi, phi ** (-2.0 / 3.0), phi ** (-1.0 / 3.0)])
+
+    def geometry(th):
+        a, dlt = th[0], th[1]
+        sa, ca, sd_, cd = np.sin(a), np.cos(a), np.sin(dlt), np.cos(dlt)
+        nhat = np.array([cd * ca, cd * sa, sd_])
+        bx, by = np.array([sa, -ca, 0.0]), np.array([-sd_ * ca, -sd_ * sa, cd])
+        xX, xY, yX, yY = d9[:, 3:6] @ bx, d9[:, 3:6] @ by, d9[:, 6:9] @ bx, d9[:, 6:9] @ by
+        u = np.stack([0.5 * (xX * xX - xY * xY - yX * yX + yY * yY), xX * xY - yX * yY], axis=1)
+        g = (u * sigma2[:, None]).T @ u
+        det = g[0, 0] * g[1, 1] - g[0, 1] ** 2
+        tr = g[0, 0] + g[1, 1]
+        if det < 1e-12 * (0.5 * tr) ** 2:
+            ev, vec = np.linalg.eigh(g)
+            chol = np.stack([vec[:, 1] / np.sqrt(ev[1]), np.zeros(2)], axis=1)      # G^-1 = e e^T / lambda
+        else:
+            chol = np.linalg.cholesky(np.array([[g[1, 1], -g[0, 1]], [-g[0, 1], g[0, 0]]]) / det)
+        # Gamma^2 = |L^T X_c|^2 + |L^T X_s|^2 with L L^T = G^-1: the detector weights u L
+        return -(d9[:, 0:3] @ nhat) / C_LIGHT, u @ chol
+
+    def run(ths):
+        b = len(ths)
+        geo = [geometry(th) for th in ths]
+        coef = torch.tensor([_chirp_coefficients(th[2], th[3], w.f_low) for th in ths], device=dev)
+        delay = torch.tensor(np.stack([g[0] for g in geo]), device=dev)
+        wts = torch.tensor(np.stack([g[1] for g in geo]), device=dev, dtype=torch.float32)
+        turns = (coef @ powers)[:, None, :] + delay[:, :, None] * f[None, None, :]
+        turns = turns - torch.round(turns)
+        q = (ybase[None] * torch.polar(torch.ones_like(turns), 2.0 * np.pi * turns)).to(torch.complex64)
+        full = torch.zeros(b, n_det, n, dtype=torch.complex64, device=dev)
+        full[:, :, sel] = q
+        del q, turns
+        z = torch.fft.ifft(full, dim=-1) * n
+        del full
+        xc = torch.einsum("bia,bit->bat", wts, z.real)
+        xs = torch.einsum("bia,bit->bat", wts, z.imag)
+        del z
+        g2 = (xc * xc + xs * xs).sum(1)
+        val, idx = g2[:, : w.n_samples].max(dim=1)
+        return val, idx
+
+    m = batch * steps
+    ths = [theta[j % len(theta)] for j in range(m)]
+    run(ths[:batch])                          # cuFFT plan and allocator warm-up
+    gpu = dev.type == "cuda"
+    if gpu:
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+    h0 = time.perf_counter()
+    outs = [run(ths[batch * s: batch * (s + 1)]) for s in range(steps)]
+    if gpu:
+        e1.record()
+        torch.cuda.synchronize(dev)
+        sec = e0.elapsed_time(e1) / 1e3
+    else:
+        sec = time.perf_counter() - h0
+    vals = torch.cat([o[0] for o in outs]).double().cpu().numpy()
+    idx = torch.cat([o[1] for o in outs]).cpu().numpy()
+    ref = np.asarray(fit_ref)[[j % len(theta) for j in range(m)]]
+    rel = float(np.max(np.abs(vals - ref) / np.abs(ref)))
+    same_tc = float(np.mean(idx == np.asarray(tc_ref)[[j % len(theta) for j in range(m)]]))
+    return {"value": round(m / sec, 2), "unit": UNIT, "particles": m,
+            "max_rel_diff_vs_fused": rel, "same_tc_fraction": same_tc,
+            "how": "torch element-wise kernels (binary64 phase) + cuFFT complex64 inverse transforms of length N "
+                   "per detector + einsum projection + max, %d particles per batch" % batch}
 
 
 def _pso_box(w):
@@ -411,39 +525,103 @@ def bench_group(fc, ranks, n_seg, dev, iters=5):
             "shapes": [{k: i[k] for k in ("n_fft", "split_bias", "k1b", "sub")} for i in shapes]}
 
 
-def cpu_baseline(w, data, theta, sample):
-    from oracle import fcas_oracle as o
-    setup = o.OracleSetup(data["det"], data["psd"], data["data"], w.n_fft, w.fs, w.f_low, w.f_high)
-    t = time.perf_counter()
-    for th in theta[:sample]:
-        o.fitness(setup, th)
-    dt = time.perf_counter() - t
-    return {"value": round(sample / dt, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{sample} particles of the same workload, FP64 numpy oracle, one thread, data preparation excluded"}
+def _oracle_worker(wname, seed, thetas, barrier, queue):
+    """One host core of the oracle baseline: the oracle's own data preparation, then one particle
+    per step, every step starting on all workers together."""
+    try:
+        from oracle import fcas_oracle as o
+        w = sd.workload_by_name(wname)
+        data = sd.make_dataset(w, seed=seed)
+        setup = o.OracleSetup(data["det"], data["psd"], data["data"], w.n_fft, w.fs, w.f_low, w.f_high)
+        times = []
+        for th in thetas:
+            barrier.wait(timeout=900)
+            t = time.perf_counter()
+            o.fitness(setup, th)
+            times.append(time.perf_counter() - t)
+        queue.put(("ok", times))
+    except Exception as e:  # reported to the parent, which then stops the pool
+        queue.put(("error", repr(e)))
+
+
+def _mem_available_bytes():
+    try:
+        with open("/proc/meminfo") as fh:
+            for line in fh:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    return None
+
+
+ORACLE_WORKER_BYTES = 3.0e9     # peak resident size of one oracle worker on the 60-min workload
+
+
+def oracle_pool(w, seed, theta, steps):
+    """Times the FP64 oracle on the host cores: one spawned single-threaded process per core (as
+    many as memory allows), each evaluating one particle per step. Returns (evals/s over all
+    steps, workers, seconds per step); a step lasts as long as its slowest worker."""
+    import multiprocessing as mp
+    n = os.cpu_count() or 1
+    avail = _mem_available_bytes()
+    if avail:
+        n = min(n, max(1, int(avail * 0.6 // (ORACLE_WORKER_BYTES if w.n_fft >= 1 << 22 else 0.5e9))))
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(n)
+    queue = ctx.Queue()
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    procs = [ctx.Process(target=_oracle_worker,
+                         args=(w.name, seed, [theta[(i + k * n) % len(theta)] for k in range(steps)], barrier, queue))
+             for i in range(n)]
+    try:
+        for p in procs:
+            p.start()
+        results = []
+        for _ in procs:
+            status, val = queue.get(timeout=1800)
+            if status != "ok":
+                raise RuntimeError("oracle worker failed: " + val)
+            results.append(val)
+    finally:
+        for p in procs:
+            p.join(timeout=5)
+            if p.is_alive():
+                p.terminate()
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    step_s = [max(r[k] for r in results) for k in range(steps)]
+    return n, step_s
+
+
+def cpu_baseline(w, seed, theta, steps):
+    n, step_s = oracle_pool(w, seed, theta, steps)
+    return {"value": round(n * steps / sum(step_s), 4), "unit": UNIT, "cores": n, "kind": "oracle",
+            "sample": f"{n * steps} particles of the same workload ({steps} per core), FP64 numpy oracle, "
+                      f"{n} single-threaded processes, data preparation excluded"}
 
 
 def bench_reference(args, ranks):
     w = sd.workload_by_name(args.workload)
     if ranks.rank != 0:          # under torchrun only rank 0 times the oracle; the others do no work
         return None
-    from oracle import fcas_oracle as o
-    data, theta = workload_inputs(w, 0)
-    setup = o.OracleSetup(data["det"], data["psd"], data["data"], w.n_fft, w.fs, w.f_low, w.f_high)
-    per_step = 1
-    for j in range(args.warmup):
-        o.fitness(setup, theta[j % len(theta)])
-    t = time.perf_counter()
-    for j in range(args.steps):
-        o.fitness(setup, theta[j % len(theta)])
-    dt = time.perf_counter() - t
-    value = per_step * args.steps / dt
+    theta = sd.make_particles(w, seed=0)
+    n, step_s = oracle_pool(w, 0, theta, args.warmup + args.steps)
+    timed = step_s[args.warmup:]
+    value = n * args.steps / sum(timed)
     return {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ranks.world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * dt / args.steps, 2),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * sum(timed) / args.steps, 2),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w.name, "n_fft": w.n_fft, "n_samples": w.n_samples,
-                       "particles_per_step": per_step},
-            "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "one particle of the workload per step, FP64 numpy oracle, one thread"},
+                       "particles_per_step": n},
+            "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": n, "kind": "oracle",
+                             "sample": f"{n} particles of the workload per step (one per core), FP64 numpy oracle, "
+                                       "single-threaded processes, data preparation excluded"},
             "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 

@@ -10,6 +10,9 @@
 // e^{S 2 pi i r (jj mod Ns) / (Ns R)}, applies the R-point DFT in registers and writes to
 // (jj / Ns) Ns R + (jj mod Ns) + r Ns. Consecutive stages exchange data through shared memory,
 // padded by one element every 16 so that the stride-16 writes of a stage do not share banks.
+// With PP the exchanges alternate between two buffers `alt` elements apart (exchange e of the
+// transform uses buffer (e + par0) mod 2): a buffer is rewritten only two exchanges after it was
+// last read, with a barrier in between, so the barrier before each write is dropped.
 // Twiddles come from a per-length table laid out stage by stage as
 //   T[(Ns - 1) + (r - 1) Ns + jm] = e^{2 pi i r jm / (Ns R)},   r = 1..R-1, jm = 0..Ns-1,
 // so that a warp reads consecutive entries; the stages together use L - 1 entries.
@@ -138,9 +141,9 @@ __device__ __forceinline__ void dft_r(C (&a)[R]) {
     }
 }
 
-template <typename Real, int S, int LOG_L, int DONE, int MAXRB>
-__device__ __forceinline__ void fftr_stage(cplx<Real> (&v)[fftr_v(LOG_L, MAXRB)], cplx<Real>* buf, int es, int j,
-                                           const cplx<Real>* __restrict__ stw) {
+template <typename Real, int S, int LOG_L, int DONE, int MAXRB, bool PP>
+__device__ __forceinline__ void fftr_stage(cplx<Real> (&v)[fftr_v(LOG_L, MAXRB)], cplx<Real>* buf0, int es, int j,
+                                           const cplx<Real>* __restrict__ stw, int alt, int par0) {
     using C = cplx<Real>;
     constexpr int L = 1 << LOG_L;
     constexpr int V = fftr_v(LOG_L, MAXRB);
@@ -151,7 +154,9 @@ __device__ __forceinline__ void fftr_stage(cplx<Real> (&v)[fftr_v(LOG_L, MAXRB)]
     constexpr int NS = 1 << DONE;
     constexpr bool FIRST = DONE == 0;
     constexpr bool LAST = DONE + RB == LOG_L;
+    constexpr int ST = DONE / MAXRB;
     if constexpr (!FIRST) {
+        const cplx<Real>* buf = (PP && ((ST - 1 + par0) & 1)) ? buf0 + alt : buf0;
         if constexpr (G % 16 == 0) {
             // pad(j + q G) = pad(j) + q (G + G/16): one base address, constant offsets
             const C* rb = buf + fft16_pad(j) * es;
@@ -207,7 +212,8 @@ __device__ __forceinline__ void fftr_stage(cplx<Real> (&v)[fftr_v(LOG_L, MAXRB)]
         for (int r = 0; r < R; ++r) v[h + r * T] = a[r];
     }
     if constexpr (!LAST) {
-        __syncthreads();
+        if constexpr (!PP) __syncthreads();
+        cplx<Real>* buf = (PP && ((ST + par0) & 1)) ? buf0 + alt : buf0;
 #pragma unroll
         for (int h = 0; h < T; ++h) {
             const int jj = j + h * G;
@@ -228,19 +234,19 @@ __device__ __forceinline__ void fftr_stage(cplx<Real> (&v)[fftr_v(LOG_L, MAXRB)]
     }
 }
 
-template <typename Real, int S, int LOG_L, int MAXRB, int DONE = 0>
+template <typename Real, int S, int LOG_L, int MAXRB, bool PP = false, int DONE = 0>
 __device__ __forceinline__ void fftr(cplx<Real> (&v)[fftr_v(LOG_L, MAXRB)], cplx<Real>* buf, int es, int j,
-                                     const cplx<Real>* __restrict__ stw) {
+                                     const cplx<Real>* __restrict__ stw, int alt = 0, int par0 = 0) {
     if constexpr (DONE < LOG_L) {
-        fftr_stage<Real, S, LOG_L, DONE, MAXRB>(v, buf, es, j, stw);
-        fftr<Real, S, LOG_L, MAXRB, DONE + fftr_radix_bits(LOG_L, DONE, MAXRB)>(v, buf, es, j, stw);
+        fftr_stage<Real, S, LOG_L, DONE, MAXRB, PP>(v, buf, es, j, stw, alt, par0);
+        fftr<Real, S, LOG_L, MAXRB, PP, DONE + fftr_radix_bits(LOG_L, DONE, MAXRB)>(v, buf, es, j, stw, alt, par0);
     }
 }
 
-template <typename Real, int S, int LOG_L>
+template <typename Real, int S, int LOG_L, bool PP = false>
 __device__ __forceinline__ void fft16(cplx<Real> (&v)[fft16_v(LOG_L)], cplx<Real>* buf, int es, int j,
-                                      const cplx<Real>* __restrict__ stw) {
-    fftr<Real, S, LOG_L, 4>(v, buf, es, j, stw);
+                                      const cplx<Real>* __restrict__ stw, int alt = 0, int par0 = 0) {
+    fftr<Real, S, LOG_L, 4, PP>(v, buf, es, j, stw, alt, par0);
 }
 
 }  // namespace fcas

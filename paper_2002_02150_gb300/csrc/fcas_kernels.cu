@@ -177,6 +177,12 @@ __device__ __forceinline__ double2 unit_phasor(double turns) {
 // W_a(t) = sum_i w_a,i Z_i(t) are the transforms of P_a (Sec. II.C projection applied before the
 // t_c scan instead of after it).
 // ------------------------------------------------------------------------------------------
+// Pass A keeps two FFT exchange buffers when both fit in 200 KB of shared memory.
+template <typename Real, int LOG_L, int K1B>
+__host__ __device__ constexpr bool pass_a_pingpong() {
+    return 2 * sizeof(cplx<Real>) * (size_t)K1B * fft16_buf_elems(LOG_L) <= 200 * 1024;
+}
+
 template <typename Real>
 struct DetConst {
     Real dh[FCAS_MAX_DET], dl[FCAS_MAX_DET], w1[FCAS_MAX_DET], w2[FCAS_MAX_DET];
@@ -300,7 +306,12 @@ pass_a_kernel(const cplx<Real>* __restrict__ y, const Basis<Real>* __restrict__ 
         for (int q = 0; q < VH; ++q) v[q] = a == 0 ? r1[q] : r2[q];
 #pragma unroll
         for (int q = VH; q < V; ++q) v[q] = mkc((Real)0, (Real)0);
-        fftr<Real, +1, LOG_L, MAXRB>(v, smem + c, K1B, j, stw);
+        // two exchange buffers where shared memory allows (no barrier before each exchange write); the
+        // exchange count is continued across the series so that a buffer is never rewritten before
+        // all its reads of the previous exchange are done
+        constexpr int NX = (LOG_L + MAXRB - 1) / MAXRB - 1;
+        fftr<Real, +1, LOG_L, MAXRB, pass_a_pingpong<Real, LOG_L, K1B>()>(v, smem + c, K1B, j, stw,
+                                                                          K1B * fft16_buf_elems(LOG_L), (a * NX) & 1);
         C* orow = out + ((p * kSeries + a) * L) * (int64_t)n1 + k1;
         // e^{2 pi i k1 ta / N} for ta = j + q G: the value at q = 0 times powers of the step e^{2 pi i k1 G / N}
         const int m0 = k1 * j, ms = k1 * G;   // < N
@@ -309,7 +320,7 @@ pass_a_kernel(const cplx<Real>* __restrict__ y, const Basis<Real>* __restrict__ 
 #pragma unroll
         for (int q = 0; q < V; ++q) {
             const int ta = j + q * G;
-            orow[(int64_t)ta * n1] = cmul(v[q], w);
+            __stcs(orow + (int64_t)ta * n1, cmul(v[q], w));   // streamed: read back only by pass B
             if (q + 1 < V) w = cmul(w, step);
         }
     }
@@ -471,7 +482,7 @@ template <typename Real, int LG, int K1B, int MAXRB = 4>
 static cudaError_t pass_a_at(const FitnessPlan& pl, const ParticleParams* params, int64_t p0, int64_t np, void* inter,
                              cudaStream_t s) {
     constexpr int THREADS = K1B * ((1 << LG) / fftr_v(LG, MAXRB));
-    const size_t smem = sizeof(cplx<Real>) * (size_t)K1B * fft16_buf_elems(LG);
+    const size_t smem = (pass_a_pingpong<Real, LG, K1B>() ? 2 : 1) * sizeof(cplx<Real>) * (size_t)K1B * fft16_buf_elems(LG);
     auto kern = pass_a_kernel<Real, LG, K1B, MAXRB>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
