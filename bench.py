@@ -233,8 +233,9 @@ def bench_ours(args, ranks):
     parts = [min(info["chunk"], n - c * info["chunk"]) for c in range(chunks_per_step)]
     mean_p = sum(parts) / len(parts)
     # pass A writes the two network-weighted series of every particle and reads the band spectrum
-    # once per launch; pass B reads the series back
-    algo = {"pass_a": mean_p * info["inter_bytes"] + d * nband * 8, "pass_b": mean_p * info["inter_bytes"]}
+    # (D complex values per bin) and the chirp basis (one float-float pair per bin) once per
+    # launch; pass B reads the series back
+    algo = {"pass_a": mean_p * info["inter_bytes"] + (d + 1) * nband * 8, "pass_b": mean_p * info["inter_bytes"]}
     peak, peak_kind = measured_peak()
     dom = max(("pass_a", "pass_b"), key=lambda k: kern[k][0])
     ms, launches = kern[dom]

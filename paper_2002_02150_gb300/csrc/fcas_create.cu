@@ -304,9 +304,8 @@ __global__ void layout_kernel(const double2* __restrict__ ynat, int n_det, int l
         }
         if (precision == FCAS_PREC_FP32) {
             BasisF bf;
-            const float h53 = (float)b53, h1 = (float)b1, h23 = (float)b23, h13 = (float)b13;
-            bf.a = make_float4(h53, (float)(b53 - (double)h53), h1, (float)(b1 - (double)h1));
-            bf.b = make_float4(h23, (float)(b23 - (double)h23), h13, (float)(b13 - (double)h13));
+            bf.h = (float)b13;
+            bf.l = (float)(b13 - (double)bf.h);
             static_cast<BasisF*>(basis)[g] = bf;
         } else {
             BasisD bd;

@@ -50,20 +50,21 @@ grad_sums_kernel(const cplx<Real>* __restrict__ y, const Basis<Real>* __restrict
             const double shift = (double)((k * t) & (n - 1)) / (double)n;   // k t / N mod 1, exact
             double qr, qi, b53, b1, b23, b13;
             if constexpr (sizeof(Real) == 4) {
-                float s = frac_mul_ff_g(pp.ch[0], pp.cl[0], b.a.x, b.a.y);
-                s += frac_mul_ff_g(pp.ch[1], pp.cl[1], b.a.z, b.a.w);
-                s += frac_mul_ff_g(pp.ch[2], pp.cl[2], b.b.x, b.b.y);
-                s += frac_mul_ff_g(pp.ch[3], pp.cl[3], b.b.z, b.b.w);
+                const ChirpPowers cpw = chirp_powers(b);
+                float s = frac_mul_ff_g(pp.ch[0], pp.cl[0], cpw.b53.x, cpw.b53.y);
+                s += frac_mul_ff_g(pp.ch[1], pp.cl[1], cpw.b1.x, cpw.b1.y);
+                s += frac_mul_ff_g(pp.ch[2], pp.cl[2], cpw.b23.x, cpw.b23.y);
+                s += frac_mul_ff_g(pp.ch[3], pp.cl[3], cpw.b13.x, cpw.b13.y);
                 float th = s + frac_mul_ff_g((float)k, 0.0f, pp.dh[i], pp.dl[i]) + (float)shift;
                 th -= rintf(th);
                 float sn, cs;
                 sincospif(2.0f * th, &sn, &cs);
                 qr = (double)(yv.x * cs - yv.y * sn);
                 qi = (double)(yv.x * sn + yv.y * cs);
-                b53 = b.a.x;
-                b1 = b.a.z;
-                b23 = b.b.x;
-                b13 = b.b.z;
+                b53 = (double)cpw.b53.x + (double)cpw.b53.y;
+                b1 = (double)cpw.b1.x + (double)cpw.b1.y;
+                b23 = (double)cpw.b23.x + (double)cpw.b23.y;
+                b13 = (double)cpw.b13.x + (double)cpw.b13.y;
             } else {
                 double th = pp.c[0] * b.a.x + pp.c[1] * b.a.y + pp.c[2] * b.b.x + pp.c[3] * b.b.y;
                 th -= rint(th);

@@ -242,10 +242,19 @@ pass_a_kernel(const cplx<Real>* __restrict__ y, const Basis<Real>* __restrict__ 
     C r1[VH], r2[VH];
 #pragma unroll
     for (int q = 0; q < VH; ++q) r1[q] = r2[q] = mkc((Real)0, (Real)0);
+    // the chirp basis of the thread's bins is requested first: its latency overlaps the detector sums
+    const Basis<Real>* bb = basis + ((int64_t)blk * (L / 2) + j) * K1B + c;
+    Basis<Real> bq[sizeof(Real) == 4 ? VH : 1];
+    if constexpr (sizeof(Real) == 4) {
+#pragma unroll
+        for (int q = 0; q < VH; ++q) bq[q] = bb[(int64_t)q * G * K1B];
+    }
     const int kbase = k1 + n1 * j;
     const int kstep = n1 * G;
     const int64_t col0 = (int64_t)blk * n_det;
-    for (int i = 0; i < n_det; ++i) {
+#pragma unroll
+    for (int i = 0; i < FCAS_MAX_DET; ++i) {
+        if (i >= n_det) break;
         C dph, dstep;
         if constexpr (sizeof(Real) == 4) {
             float fb = frac_mul_ff((float)kbase, 0.0f, sc.dh[i], sc.dl[i]);
@@ -280,19 +289,18 @@ pass_a_kernel(const cplx<Real>* __restrict__ y, const Basis<Real>* __restrict__ 
                 cfl[r] = pp->cl[r];
             }
         }
-        const Basis<Real>* bb = basis + ((int64_t)blk * (L / 2) + j) * K1B + c;
 #pragma unroll
         for (int q = 0; q < VH; ++q) {
-            const Basis<Real> b = bb[(int64_t)q * G * K1B];
             C cp;
             if constexpr (sizeof(Real) == 4) {
-                float s = frac_mul_ff(cfh[0], cfl[0], b.a.x, b.a.y);
-                s += frac_mul_ff(cfh[1], cfl[1], b.a.z, b.a.w);
-                s += frac_mul_ff(cfh[2], cfl[2], b.b.x, b.b.y);
-                s += frac_mul_ff(cfh[3], cfl[3], b.b.z, b.b.w);
+                const ChirpPowers b = chirp_powers(bq[q]);
+                float s = frac_mul_ff(cfh[0], cfl[0], b.b53.x, b.b53.y);
+                s += frac_mul_ff(cfh[1], cfl[1], b.b1.x, b.b1.y);
+                s += frac_mul_ff(cfh[2], cfl[2], b.b23.x, b.b23.y);
+                s += frac_mul_ff(cfh[3], cfl[3], b.b13.x, b.b13.y);
                 cp = fast_phasor(s - rintf(s));
             } else {
-                cp = unit_phasor(chirp_frac(b, *pp));
+                cp = unit_phasor(chirp_frac(bb[(int64_t)q * G * K1B], *pp));
             }
             r1[q] = cmul(r1[q], cp);
             r2[q] = cmul(r2[q], cp);

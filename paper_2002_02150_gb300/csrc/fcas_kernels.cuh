@@ -6,11 +6,45 @@
 
 namespace fcas {
 
-// Float-float chirp-phase basis phi^-5/3, phi^-1, phi^-2/3, phi^-1/3 of one bin (hi, lo pairs).
-struct __align__(16) BasisF {
-    float4 a;   // (b53 hi, b53 lo, b1 hi, b1 lo)
-    float4 b;   // (b23 hi, b23 lo, b13 hi, b13 lo)
+// Chirp-phase basis of one bin for the FP32 form: phi^-1/3 as a float-float pair (hi, lo); the
+// powers phi^-2/3, phi^-1, phi^-5/3 are formed from it by float-float products.
+struct __align__(8) BasisF {
+    float h, l;
 };
+
+// (ah + al)(bh + bl) as a float-float pair: the exact leading product by a fused multiply-add,
+// the cross terms added to its error, then renormalised (double-word product, relative error a
+// few units of 2^-48).
+__host__ __device__ __forceinline__ float2 ff_mul(float ah, float al, float bh, float bl) {
+#ifdef __CUDA_ARCH__
+    const float p = __fmul_rn(ah, bh);
+    float e = __fmaf_rn(ah, bh, -p);
+    e = __fmaf_rn(ah, bl, e);
+    e = __fmaf_rn(al, bh, e);
+    const float hi = __fadd_rn(p, e);
+    return make_float2(hi, __fsub_rn(e, __fsub_rn(hi, p)));
+#else
+    const float p = ah * bh;
+    float e = fmaf(ah, bh, -p);
+    e = fmaf(ah, bl, e);
+    e = fmaf(al, bh, e);
+    const float hi = p + e;
+    return make_float2(hi, e - (hi - p));
+#endif
+}
+
+// phi^-5/3, phi^-1, phi^-2/3, phi^-1/3 (hi, lo pairs) of a bin from its basis t = phi^-1/3
+struct ChirpPowers {
+    float2 b53, b1, b23, b13;
+};
+__host__ __device__ __forceinline__ ChirpPowers chirp_powers(const BasisF& t) {
+    ChirpPowers r;
+    r.b13 = make_float2(t.h, t.l);
+    r.b23 = ff_mul(t.h, t.l, t.h, t.l);
+    r.b1 = ff_mul(r.b23.x, r.b23.y, t.h, t.l);
+    r.b53 = ff_mul(r.b1.x, r.b1.y, r.b23.x, r.b23.y);
+    return r;
+}
 struct __align__(16) BasisD {
     double2 a;  // (b53, b1)
     double2 b;  // (b23, b13)
