@@ -91,6 +91,17 @@ int fcas_create(fcas_ctx** out, const fcas_setup* setup, const fcas_detector* de
                 const double* psd, const double* data, void* stream);
 
 /*
+ * fcas_create_time_shifted -- fcas_create on a time-shifted copy of the data: detector i's series is
+ * first shifted circularly within its n_samples samples, x'_i[t] = x_i[(t - shifts[i]) mod n_samples]
+ * (shifts taken modulo n_samples, negative values allowed). Sec. V generates background noise
+ * realisations this way: unphysical relative shifts (>= 10 s there) between the detectors' series
+ * of one data realisation. The caller's data is not modified. shifts: host array [n_det]; other
+ * arguments, errors and synchronisation as fcas_create (FCAS_ERR_INVALID for NULL shifts).
+ */
+int fcas_create_time_shifted(fcas_ctx** out, const fcas_setup* setup, const fcas_detector* det, const double* psd,
+                             const double* data, const int64_t* shifts, void* stream);
+
+/*
  * fcas_fitness -- coherent fitness of a batch of particles (Sec. II.C, eq. gammaSqd).
  *   n       : number of particles (0 is a no-op).
  *   theta   : [n][4] = (alpha [rad, ECEF azimuth], delta [rad, latitude in -pi/2..pi/2],
@@ -262,7 +273,31 @@ int fcas_group_create(fcas_group** out, int32_t n_ctx, fcas_ctx* const* ctxs, in
  */
 int fcas_group_search(fcas_group* group, const fcas_pso_config* cfg, fcas_search_result* results, void* stream);
 
+/*
+ * fcas_group_search_boxes -- fcas_group_search with one PSO box per segment: segment s searches
+ * boxes[8 s .. 8 s + 7] (the layout of fcas_pso_config.box) instead of cfg->box, with the same
+ * per-segment random-number key. A context may appear in a group several times, so one data
+ * segment can be searched over several rectangles of the (tau0, tau1.5) plane together (Sec. IV:
+ * the rectangles covering the chirp-time range are searched in parallel, their number does not
+ * add to the run time). boxes: host array [n_ctx][8]; each box is validated like cfg->box
+ * (FCAS_ERR_INVALID names the segment). results: host array [n_ctx][n_runs]. Synchronous.
+ */
+int fcas_group_search_boxes(fcas_group* group, const fcas_pso_config* cfg, const double* boxes,
+                            fcas_search_result* results, void* stream);
+
 void fcas_group_destroy(fcas_group* group);
+
+/*
+ * fcas_tau_tiles -- n0 x n15 overlapping rectangles covering [tau0_lo, tau0_hi] x [tau15_lo, tau15_hi]
+ * (Sec. IV: a set of rectangles with an overlap fraction covers the chirp-time range). Along each
+ * axis the n tiles have width w = (hi - lo) / (n - (n - 1) overlap) and tile j starts at
+ * lo + j (1 - overlap) w, so neighbours share the fraction `overlap` of a width and the last tile
+ * ends at hi. Written as PSO boxes over the whole sky (alpha in [0, 2 pi], delta in [-pi/2, pi/2])
+ * to boxes[8 (j0 n15 + j15) ...], j0 the tau0 index. Needs 0 < lo < hi on both axes, n0, n15 >= 1,
+ * 0 <= overlap < 1 (FCAS_ERR_INVALID otherwise). boxes: host array [n0 n15][8]. Host only.
+ */
+int fcas_tau_tiles(double tau0_lo, double tau0_hi, double tau15_lo, double tau15_hi, int32_t n0, int32_t n15,
+                   double overlap, double* boxes);
 
 /* Release every resource held by the context (NULL is a no-op). Synchronises the device. */
 void fcas_destroy(fcas_ctx* ctx);

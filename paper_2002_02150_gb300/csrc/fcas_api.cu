@@ -217,6 +217,9 @@ int apply_layout(fcas_ctx* c, int bias, int k1b, int sub, int radix_bits_a, cuda
 
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
+int create_impl(fcas_ctx** out, const fcas_setup* setup, const fcas_detector* det, const double* psd,
+                const double* data, const int64_t* shifts, void* stream);
+
 }  // namespace
 
 extern "C" {
@@ -227,6 +230,22 @@ int fcas_version(void) { return 100; }
 
 int fcas_create(fcas_ctx** out, const fcas_setup* setup, const fcas_detector* det, const double* psd,
                 const double* data, void* stream) {
+    return create_impl(out, setup, det, psd, data, nullptr, stream);
+}
+
+int fcas_create_time_shifted(fcas_ctx** out, const fcas_setup* setup, const fcas_detector* det, const double* psd,
+                             const double* data, const int64_t* shifts, void* stream) {
+    g_last_error.clear();
+    if (!shifts) return fail(FCAS_ERR_INVALID, "fcas_create_time_shifted: NULL shifts");
+    return create_impl(out, setup, det, psd, data, shifts, stream);
+}
+
+}  // extern "C"
+
+namespace {
+
+int create_impl(fcas_ctx** out, const fcas_setup* setup, const fcas_detector* det, const double* psd,
+                const double* data, const int64_t* shifts, void* stream) {
     g_last_error.clear();
     if (!out || !setup || !det || !psd || !data) return fail(FCAS_ERR_INVALID, "fcas_create: NULL argument");
     *out = nullptr;
@@ -286,10 +305,12 @@ int fcas_create(fcas_ctx** out, const fcas_setup* setup, const fcas_detector* de
     double2* d_work = nullptr;
     double* d_psd = nullptr;
     double* d_data = nullptr;
+    double* d_shifted = nullptr;
     int* d_flag = nullptr;
     double* d_sig = nullptr;
     const bool psd_dev = is_device_ptr(psd), data_dev = is_device_ptr(data);
     auto cleanup = [&](int code) {
+        if (d_shifted) cudaFree(d_shifted);
         if (d_spec) cudaFree(d_spec);
         if (d_work) cudaFree(d_work);
         if (d_psd && !psd_dev) cudaFree(d_psd);
@@ -324,9 +345,18 @@ int fcas_create(fcas_ctx** out, const fcas_setup* setup, const fcas_detector* de
         FCAS_TRYCUDA(cudaMemcpyAsync(d_data, data, sizeof(double) * (size_t)D * s.n_samples, cudaMemcpyHostToDevice,
                                      st));
     }
+    if (shifts) {
+        // background realisation: each detector's series shifted circularly (the caller's data is
+        // left untouched)
+        DetShifts sh{};
+        for (int i = 0; i < D; ++i) sh.s[i] = ((shifts[i] % s.n_samples) + s.n_samples) % s.n_samples;
+        FCAS_TRY(dev_alloc(&d_shifted, sizeof(double) * (size_t)D * s.n_samples, "time-shifted data"));
+        FCAS_TRYCUDA(launch_time_shift(d_data, d_shifted, D, s.n_samples, sh, st));
+    }
+    const double* d_use = shifts ? d_shifted : d_data;
     FCAS_TRY(dev_alloc(&d_flag, sizeof(int), "flag"));
     FCAS_TRYCUDA(cudaMemsetAsync(d_flag, 0, sizeof(int), st));
-    FCAS_TRYCUDA(launch_check_finite(d_data, (int64_t)D * s.n_samples, d_flag, st));
+    FCAS_TRYCUDA(launch_check_finite(d_use, (int64_t)D * s.n_samples, d_flag, st));
     FCAS_TRYCUDA(launch_check_psd(d_psd, D, psd_row, k_lo, k_hi, d_flag, st));
     int h_flag = 0;
     FCAS_TRYCUDA(cudaMemcpyAsync(&h_flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -376,7 +406,7 @@ int fcas_create(fcas_ctx** out, const fcas_setup* setup, const fcas_detector* de
     // forward FFT of the data (binary64) and the whitened, re-laid-out band spectrum
     FCAS_TRY(dev_alloc(&d_spec, sizeof(double2) * (size_t)D * n, "data spectrum"));
     FCAS_TRY(dev_alloc(&d_work, sizeof(double2) * (size_t)D * n, "data FFT work"));
-    FCAS_TRYCUDA(launch_data_fft(d_data, D, s.n_samples, log_n, c->log_n1, c->log_n2, c->d_tw64, log_tw - c->log_n2,
+    FCAS_TRYCUDA(launch_data_fft(d_use, D, s.n_samples, log_n, c->log_n1, c->log_n2, c->d_tw64, log_tw - c->log_n2,
                                  log_tw - c->log_n1, c->d_twlo64, c->d_twhi64, d_work, d_spec, st));
     const size_t half = (size_t)(n / 2);
     FCAS_TRY(dev_alloc(&c->d_ynat, sizeof(double2) * (size_t)D * half, "whitened spectrum (natural order)"));
@@ -415,6 +445,10 @@ int fcas_create(fcas_ctx** out, const fcas_setup* setup, const fcas_detector* de
     *out = c;
     return FCAS_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 int fcas_fitness(fcas_ctx* c, int64_t n, const double* theta, double* fitness, int64_t* tc, void* stream) {
     g_last_error.clear();
@@ -755,12 +789,26 @@ int fcas_group_create(fcas_group** out, int32_t n_ctx, fcas_ctx* const* ctxs, in
 }
 
 int fcas_group_search(fcas_group* g, const fcas_pso_config* cfg, fcas_search_result* results, void* stream) {
+    return fcas_group_search_boxes(g, cfg, nullptr, results, stream);
+}
+
+int fcas_group_search_boxes(fcas_group* g, const fcas_pso_config* cfg, const double* boxes,
+                            fcas_search_result* results, void* stream) {
     g_last_error.clear();
     if (!g || !results) return fail(FCAS_ERR_INVALID, "fcas_group_search: NULL argument");
     char msg[256];
     int rc = pso_validate(cfg, msg, sizeof(msg));
     if (rc) return fail(rc, "fcas_group_search: %s", msg);
     const int n_ctx = (int)g->ctxs.size();
+    std::vector<fcas_pso_config> cfgs(n_ctx, *cfg);
+    for (int i = 0; i < n_ctx; ++i) {
+        cfgs[i].seed = segment_seed(cfg->seed, i);
+        if (boxes) {
+            for (int d = 0; d < 8; ++d) cfgs[i].box[d] = boxes[8 * i + d];
+            rc = pso_validate(&cfgs[i], msg, sizeof(msg));
+            if (rc) return fail(rc, "fcas_group_search_boxes: segment %d: %s", i, msg);
+        }
+    }
     const int64_t rows = (int64_t)cfg->n_runs * cfg->n_particles;
     if (rows > g->params_cap) {
         if (g->d_params) cudaFree(g->d_params);
@@ -783,9 +831,7 @@ int fcas_group_search(fcas_group* g, const fcas_pso_config* cfg, fcas_search_res
     std::vector<PsoDev> gs(n_ctx);
     for (int i = 0; i < n_ctx; ++i) {
         ws[i] = carve_swarm(g->d_pso + per * i, rows, cfg->n_runs);
-        fcas_pso_config ci = *cfg;
-        ci.seed = segment_seed(cfg->seed, i);
-        gs[i] = pso_dev(&ci);
+        gs[i] = pso_dev(&cfgs[i]);
     }
     cudaStream_t st = g->st;
     cudaEvent_t ev;
@@ -811,6 +857,34 @@ int fcas_group_search(fcas_group* g, const fcas_pso_config* cfg, fcas_search_res
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaEventDestroy(ev);
     if (e != cudaSuccess) return fail(FCAS_ERR_CUDA, "fcas_group_search: %s", cudaGetErrorString(e));
+    return FCAS_OK;
+}
+
+int fcas_tau_tiles(double tau0_lo, double tau0_hi, double tau15_lo, double tau15_hi, int32_t n0, int32_t n15,
+                   double overlap, double* boxes) {
+    g_last_error.clear();
+    if (!boxes) return fail(FCAS_ERR_INVALID, "fcas_tau_tiles: NULL boxes");
+    if (n0 < 1 || n15 < 1) return fail(FCAS_ERR_INVALID, "fcas_tau_tiles: need n0, n15 >= 1");
+    if (!(overlap >= 0.0 && overlap < 1.0)) return fail(FCAS_ERR_INVALID, "fcas_tau_tiles: need 0 <= overlap < 1");
+    if (!(std::isfinite(tau0_lo) && std::isfinite(tau0_hi) && std::isfinite(tau15_lo) && std::isfinite(tau15_hi) &&
+          tau0_lo > 0.0 && tau15_lo > 0.0 && tau0_hi > tau0_lo && tau15_hi > tau15_lo))
+        return fail(FCAS_ERR_INVALID, "fcas_tau_tiles: need finite 0 < lo < hi on both axes");
+    const double w0 = (tau0_hi - tau0_lo) / ((double)n0 - (double)(n0 - 1) * overlap);
+    const double w15 = (tau15_hi - tau15_lo) / ((double)n15 - (double)(n15 - 1) * overlap);
+    const double kPi = 3.14159265358979323846;
+    for (int a = 0; a < n0; ++a) {
+        for (int b = 0; b < n15; ++b) {
+            double* bx = boxes + 8 * ((int64_t)a * n15 + b);
+            bx[0] = 0.0;
+            bx[1] = 2.0 * kPi;
+            bx[2] = -0.5 * kPi;
+            bx[3] = 0.5 * kPi;
+            bx[4] = tau0_lo + a * (1.0 - overlap) * w0;
+            bx[5] = a == n0 - 1 ? tau0_hi : bx[4] + w0;
+            bx[6] = tau15_lo + b * (1.0 - overlap) * w15;
+            bx[7] = b == n15 - 1 ? tau15_hi : bx[6] + w15;
+        }
+    }
     return FCAS_OK;
 }
 

@@ -55,6 +55,29 @@ __global__ void check_finite_kernel(const double* __restrict__ x, int64_t n, int
         if (!isfinite(x[i])) atomicOr(flag, 1);
 }
 
+// Circular time shift of each detector's series within its n samples: y_i[t] = x_i[(t - s_i) mod n]
+// (shifts already reduced to 0..n-1). Background realisations of Sec. V.
+__global__ void time_shift_kernel(const double* __restrict__ x, double* __restrict__ y, int n_det, int64_t n,
+                                  DetShifts sh) {
+    const int64_t total = (int64_t)n_det * n;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(g / n);
+        const int64_t t = g - (int64_t)i * n;
+        int64_t src = t - sh.s[i];
+        if (src < 0) src += n;
+        y[g] = x[(int64_t)i * n + src];
+    }
+}
+
+cudaError_t launch_time_shift(const double* x, double* y, int n_det, int64_t n, const DetShifts& sh, cudaStream_t s) {
+    const int64_t total = (int64_t)n_det * n;
+    if (total <= 0) return cudaSuccess;
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 8192) blocks = 8192;
+    time_shift_kernel<<<(unsigned)blocks, 256, 0, s>>>(x, y, n_det, n, sh);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_check_finite(const double* x, int64_t n, int* flag, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     int64_t blocks = (n + 255) / 256;

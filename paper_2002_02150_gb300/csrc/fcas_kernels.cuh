@@ -111,6 +111,10 @@ cudaError_t launch_grad_final(const double* theta, const int64_t* tc, int64_t n,
 cudaError_t launch_tables(int log_n, int log_n1, int log_n2, double2* tw64, double2* twlo64, double2* twhi64,
                           float2* tw32, float2* twlo32, float2* twhi32, cudaStream_t s);
 cudaError_t launch_check_finite(const double* x, int64_t n, int* flag, cudaStream_t s);
+struct DetShifts {
+    int64_t s[FCAS_MAX_DET];   // circular shift of each detector's series, 0..n_samples-1
+};
+cudaError_t launch_time_shift(const double* x, double* y, int n_det, int64_t n, const DetShifts& sh, cudaStream_t s);
 cudaError_t launch_check_psd(const double* psd, int n_det, int64_t row, int64_t k_lo, int64_t k_hi, int* flag,
                              cudaStream_t s);
 cudaError_t launch_sigma2(const double* psd, int n_det, int64_t row, int64_t k_lo, int64_t k_hi, double df,

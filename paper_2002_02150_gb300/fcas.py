@@ -116,6 +116,14 @@ def load_library():
     lib.fcas_group_search.restype = i32
     lib.fcas_group_destroy.argtypes = [vp]
     lib.fcas_group_destroy.restype = None
+    lib.fcas_create_time_shifted.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(fcas_setup),
+                                             ctypes.POINTER(fcas_detector), vp, vp, ctypes.POINTER(i64), vp]
+    lib.fcas_create_time_shifted.restype = i32
+    lib.fcas_group_search_boxes.argtypes = [vp, ctypes.POINTER(fcas_pso_config), ctypes.POINTER(dp),
+                                            ctypes.POINTER(fcas_search_result), vp]
+    lib.fcas_group_search_boxes.restype = i32
+    lib.fcas_tau_tiles.argtypes = [dp, dp, dp, dp, ctypes.c_int32, ctypes.c_int32, dp, ctypes.POINTER(dp)]
+    lib.fcas_tau_tiles.restype = i32
     _lib = lib
     return lib
 
@@ -183,8 +191,10 @@ class Context:
 FCAS_SETUP_LAZY_SCRATCH = 1
 
 
-def fcas_create(det, psd, data, n_fft, fs, f_low, f_high, precision="fp32", max_batch=0, stream=None, flags=0):
-    """Prepare a data segment. det: (D, 9) ECEF r, x arm, y arm; psd: (D, n_fft/2+1); data: (D, n_samples)."""
+def fcas_create(det, psd, data, n_fft, fs, f_low, f_high, precision="fp32", max_batch=0, stream=None, flags=0,
+                shifts=None):
+    """Prepare a data segment. det: (D, 9) ECEF r, x arm, y arm; psd: (D, n_fft/2+1); data: (D, n_samples).
+    shifts: optional (D,) circular time shifts in samples (fcas_create_time_shifted)."""
     lib = load_library()
     det = np.asarray(det, dtype=np.float64).reshape(-1, 9)
     n_det = det.shape[0]
@@ -200,7 +210,16 @@ def fcas_create(det, psd, data, n_fft, fs, f_low, f_high, precision="fp32", max_
     p_psd, k1 = _ptr(psd, np.float64)
     p_data, k2 = _ptr(data, np.float64)
     handle = ctypes.c_void_p()
-    _check(lib.fcas_create(ctypes.byref(handle), ctypes.byref(setup), dets, p_psd, p_data, _stream(stream, psd, data)))
+    if shifts is None:
+        _check(lib.fcas_create(ctypes.byref(handle), ctypes.byref(setup), dets, p_psd, p_data,
+                               _stream(stream, psd, data)))
+    else:
+        sh = np.asarray(shifts, dtype=np.int64).reshape(-1)
+        if sh.size != n_det:
+            raise ValueError(f"shifts must have one entry per detector ({n_det})")
+        arr = (ctypes.c_int64 * n_det)(*[int(v) for v in sh])
+        _check(lib.fcas_create_time_shifted(ctypes.byref(handle), ctypes.byref(setup), dets, p_psd, p_data, arr,
+                                            _stream(stream, psd, data)))
     return Context(handle, setup)
 
 
@@ -420,12 +439,20 @@ class Group:
         self.handle = ctypes.c_void_p()
         _check(load_library().fcas_group_create(ctypes.byref(self.handle), len(self.contexts), arr, int(max_batch)))
 
-    def search(self, cfg, stream=None):
-        """Returns a list (per segment) of lists (per run) of result dicts."""
+    def search(self, cfg, stream=None, boxes=None):
+        """Returns a list (per segment) of lists (per run) of result dicts. boxes: optional (n_ctx, 8)
+        PSO box per segment (fcas_group_search_boxes)."""
         n = len(self.contexts)
         res = (fcas_search_result * (n * cfg.n_runs))()
         s = ctypes.c_void_p(int(stream)) if stream is not None else ctypes.c_void_p(0)
-        _check(load_library().fcas_group_search(self.handle, ctypes.byref(cfg), res, s))
+        if boxes is None:
+            _check(load_library().fcas_group_search(self.handle, ctypes.byref(cfg), res, s))
+        else:
+            b = np.ascontiguousarray(np.asarray(boxes, dtype=np.float64).reshape(-1))
+            if b.size != 8 * n:
+                raise ValueError(f"boxes must be ({n}, 8)")
+            _check(load_library().fcas_group_search_boxes(self.handle, ctypes.byref(cfg),
+                                                          b.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), res, s))
         out = [dict(fitness=r.fitness, theta=list(r.theta), tc=r.tc, evaluations=r.evaluations) for r in res]
         return [out[i * cfg.n_runs:(i + 1) * cfg.n_runs] for i in range(n)]
 
@@ -454,3 +481,29 @@ def fcas_group_create(contexts, max_batch=0):
 def segment_seed(seed, s):
     """Key of segment s's swarm in a group search (seed + s * 0x9E3779B97F4A7C15 mod 2^64)."""
     return (int(seed) + s * 0x9E3779B97F4A7C15) & 0xFFFFFFFFFFFFFFFF
+
+
+def fcas_tau_tiles(tau0_lo, tau0_hi, tau15_lo, tau15_hi, n0, n15, overlap=0.0):
+    """(n0 * n15, 8) PSO boxes over the whole sky tiling the chirp-time rectangle with the given
+    overlap fraction (C: fcas_tau_tiles; host only)."""
+    out = np.zeros((int(n0) * int(n15), 8))
+    _check(load_library().fcas_tau_tiles(float(tau0_lo), float(tau0_hi), float(tau15_lo), float(tau15_hi), int(n0),
+                                         int(n15), float(overlap), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return out
+
+
+def time_slide_background(det, psd, data, n_fft, fs, f_low, f_high, shifts, cfg, precision="fp32", max_batch=0,
+                          stream=None):
+    """Background of the search statistic from time-shifted copies of one data realisation (Sec. V):
+    one context per row of shifts (S, D) (fcas_create_time_shifted, lazy scratch), all searched
+    together by one group with cfg. Returns (best fitness per slide (S,), per-slide run results)."""
+    ctxs = [fcas_create(det, psd, data, n_fft, fs, f_low, f_high, precision=precision, stream=stream,
+                        flags=FCAS_SETUP_LAZY_SCRATCH, shifts=row) for row in np.asarray(shifts)]
+    try:
+        with Group(ctxs, max_batch=max_batch) as g:
+            res = g.search(cfg, stream=stream)
+    finally:
+        for c in ctxs:
+            c.close()
+    best = np.array([max(r["fitness"] for r in seg) for seg in res])
+    return best, res
