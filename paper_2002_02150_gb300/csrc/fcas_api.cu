@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "fcas_ctx.cuh"
 #include "fcas_kernels.cuh"
 #include "fcas_pso.cuh"
@@ -15,6 +17,16 @@
 using namespace fcas;
 
 namespace {
+
+// Host-side NVTX range around each C entry point (visible to ncu --nvtx and other NVTX tools;
+// a no-op when no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 
 thread_local std::string g_last_error;
 
@@ -230,11 +242,13 @@ int fcas_version(void) { return 100; }
 
 int fcas_create(fcas_ctx** out, const fcas_setup* setup, const fcas_detector* det, const double* psd,
                 const double* data, void* stream) {
+    NvtxRange nvtx_("fcas_create");
     return create_impl(out, setup, det, psd, data, nullptr, stream);
 }
 
 int fcas_create_time_shifted(fcas_ctx** out, const fcas_setup* setup, const fcas_detector* det, const double* psd,
                              const double* data, const int64_t* shifts, void* stream) {
+    NvtxRange nvtx_("fcas_create_time_shifted");
     g_last_error.clear();
     if (!shifts) return fail(FCAS_ERR_INVALID, "fcas_create_time_shifted: NULL shifts");
     return create_impl(out, setup, det, psd, data, shifts, stream);
@@ -451,6 +465,7 @@ int create_impl(fcas_ctx** out, const fcas_setup* setup, const fcas_detector* de
 extern "C" {
 
 int fcas_fitness(fcas_ctx* c, int64_t n, const double* theta, double* fitness, int64_t* tc, void* stream) {
+    NvtxRange nvtx_("fcas_fitness");
     g_last_error.clear();
     if (!c) return fail(FCAS_ERR_INVALID, "fcas_fitness: NULL context");
     if (n < 0) return fail(FCAS_ERR_INVALID, "fcas_fitness: n < 0");
@@ -574,6 +589,7 @@ uint64_t segment_seed(uint64_t seed, int s) { return seed + (uint64_t)s * 0x9E37
 extern "C" {
 
 int fcas_search(fcas_ctx* c, const fcas_pso_config* cfg, fcas_search_result* results, void* stream) {
+    NvtxRange nvtx_("fcas_search");
     g_last_error.clear();
     if (!c || !results) return fail(FCAS_ERR_INVALID, "fcas_search: NULL argument");
     char msg[256];
@@ -618,6 +634,7 @@ int fcas_search(fcas_ctx* c, const fcas_pso_config* cfg, fcas_search_result* res
 }
 
 int fcas_autotune(fcas_ctx* c, int64_t n_particles, const char* cache_path, void* stream) {
+    NvtxRange nvtx_("fcas_autotune");
     g_last_error.clear();
     if (!c) return fail(FCAS_ERR_INVALID, "fcas_autotune: NULL context");
     if (n_particles < 1) return fail(FCAS_ERR_INVALID, "fcas_autotune: n_particles < 1");
@@ -794,6 +811,7 @@ int fcas_group_search(fcas_group* g, const fcas_pso_config* cfg, fcas_search_res
 
 int fcas_group_search_boxes(fcas_group* g, const fcas_pso_config* cfg, const double* boxes,
                             fcas_search_result* results, void* stream) {
+    NvtxRange nvtx_("fcas_group_search");
     g_last_error.clear();
     if (!g || !results) return fail(FCAS_ERR_INVALID, "fcas_group_search: NULL argument");
     char msg[256];
@@ -899,6 +917,7 @@ void fcas_group_destroy(fcas_group* g) {
 }
 
 int fcas_gradient(fcas_ctx* c, int64_t n, const double* theta, const int64_t* tc, double* grad, void* stream) {
+    NvtxRange nvtx_("fcas_gradient");
     g_last_error.clear();
     if (!c) return fail(FCAS_ERR_INVALID, "fcas_gradient: NULL context");
     if (n < 0) return fail(FCAS_ERR_INVALID, "fcas_gradient: n < 0");
