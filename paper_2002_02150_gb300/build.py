@@ -41,10 +41,16 @@ def build(verbose=False, force=False, defines=(), out=None):
     preprocessor `defines` for launch-shape tuning). Returns the library path."""
     if defines or out:
         build_dir = BUILD + "_" + hashlib.sha1(" ".join(defines).encode()).hexdigest()[:8]
+        target = out or LIB
+        if not force and out and os.path.exists(target):
+            srcs = [os.path.join(CSRC, s) for s in SOURCES]
+            hdrs = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".cuh", ".h"))]
+            hdrs.append(os.path.join(HERE, "..", "include", "fcas.h"))
+            if os.path.getmtime(target) >= max(os.path.getmtime(p) for p in srcs + hdrs + [__file__]):
+                return target
         os.makedirs(build_dir, exist_ok=True)
         with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
             objs = list(ex.map(lambda s: _compile(s, verbose, defines, build_dir), SOURCES))
-        target = out or LIB
         r = subprocess.run([_nvcc(), *ARCH, "-shared", "-o", target + ".tmp", *objs, "-lcudart"], capture_output=True,
                            text=True)
         if r.returncode != 0:

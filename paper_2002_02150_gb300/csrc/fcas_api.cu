@@ -505,6 +505,8 @@ int fcas_fitness(fcas_ctx* c, int64_t n, const double* theta, double* fitness, i
     if (!f_dev) FCAS_CUDA(cudaMemcpyAsync(fitness, d_fit, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, st));
     if (!t_dev) FCAS_CUDA(cudaMemcpyAsync(tc, d_tc, sizeof(int64_t) * (size_t)n, cudaMemcpyDeviceToHost, st));
     if (!th_dev || !f_dev || !t_dev) FCAS_CUDA(cudaStreamSynchronize(st));
+    if (const unsigned int bad = take_index_checks(st))
+        return fail(FCAS_ERR_CUDA, "fcas_fitness: index checks failed (bits 0x%x)", bad);
     return FCAS_OK;
 }
 

@@ -32,6 +32,22 @@ __host__ __device__ constexpr int fft16_v(int log_l) { return fftr_v(log_l, 4); 
 __host__ __device__ constexpr int fft16_pad(int e) { return e + (e >> 4); }
 __host__ __device__ constexpr int fft16_buf_elems(int log_l) { return fft16_pad(1 << log_l); }
 
+// Checked build (FCAS_CHECKED): the fitness kernels recompute each shared-memory, table and global
+// index from its definition and range-test it; a failed test sets bit `bit` of this flag (read and
+// cleared by the host after the launches) and the access is skipped. No trap, no fault.
+#ifdef FCAS_CHECKED
+static __device__ unsigned int g_index_checks;
+__device__ __forceinline__ bool index_check(bool ok, int bit) {
+    if (!ok) atomicOr(&g_index_checks, 1u << bit);
+    return ok;
+}
+#define FCAS_CHECK(cond, bit) ::fcas::index_check((cond), (bit))
+#else
+#define FCAS_CHECK(cond, bit) true
+#endif
+enum IndexCheck { kCheckExchangeRead = 0, kCheckExchangeWrite = 1, kCheckTwiddle = 2, kCheckSpectrum = 3,
+                  kCheckBasis = 4, kCheckInterWrite = 5, kCheckInterRead = 6 };
+
 template <int S, typename C>
 __device__ __forceinline__ void r16_dft4(C& a0, C& a1, C& a2, C& a3) {
     C t0 = a0 + a2, t1 = a0 - a2, t2 = a1 + a3, t3 = a1 - a3;
@@ -161,10 +177,16 @@ __device__ __forceinline__ void fftr_stage(cplx<Real> (&v)[fftr_v(LOG_L, MAXRB)]
             // pad(j + q G) = pad(j) + q (G + G/16): one base address, constant offsets
             const C* rb = buf + fft16_pad(j) * es;
 #pragma unroll
-            for (int q = 0; q < V; ++q) v[q] = rb[q * (G + G / 16) * es];
+            for (int q = 0; q < V; ++q) {
+                const int e = fft16_pad(j) + q * (G + G / 16);
+                if (FCAS_CHECK(e == fft16_pad(j + q * G) && e < fft16_buf_elems(LOG_L), kCheckExchangeRead))
+                    v[q] = rb[q * (G + G / 16) * es];
+            }
         } else {
 #pragma unroll
-            for (int q = 0; q < V; ++q) v[q] = buf[fft16_pad(j + q * G) * es];
+            for (int q = 0; q < V; ++q)
+                if (FCAS_CHECK(fft16_pad(j + q * G) < fft16_buf_elems(LOG_L), kCheckExchangeRead))
+                    v[q] = buf[fft16_pad(j + q * G) * es];
         }
     }
 #pragma unroll
@@ -178,8 +200,11 @@ __device__ __forceinline__ void fftr_stage(cplx<Real> (&v)[fftr_v(LOG_L, MAXRB)]
             const C* t = stw + (NS - 1) + jm;
             if constexpr (R >= 8) {
                 // w^r for r = 1..R-1 from two table entries: w and w^4 (powers by products, <= 3 roundings)
-                C w1 = __ldg(t);
-                C w4 = __ldg(t + 3 * NS);
+                C w1 = mkc((Real)1, (Real)0), w4 = w1;
+                if (FCAS_CHECK((NS - 1) + jm + 3 * NS < L, kCheckTwiddle)) {
+                    w1 = __ldg(t);
+                    w4 = __ldg(t + 3 * NS);
+                }
                 if constexpr (S < 0) {
                     w1 = cconj(w1);
                     w4 = cconj(w4);
@@ -201,7 +226,8 @@ __device__ __forceinline__ void fftr_stage(cplx<Real> (&v)[fftr_v(LOG_L, MAXRB)]
             } else {
 #pragma unroll
                 for (int r = 1; r < R; ++r) {
-                    C w = __ldg(t + (r - 1) * NS);
+                    C w = mkc((Real)1, (Real)0);
+                    if (FCAS_CHECK((NS - 1) + (r - 1) * NS + jm < L, kCheckTwiddle)) w = __ldg(t + (r - 1) * NS);
                     if constexpr (S < 0) w = cconj(w);
                     a[r] = cmul(a[r], w);
                 }
@@ -224,10 +250,16 @@ __device__ __forceinline__ void fftr_stage(cplx<Real> (&v)[fftr_v(LOG_L, MAXRB)]
             if constexpr (NS % 16 == 0 || (16 % NS == 0 && (NS * R) % 16 == 0) || (NS == 1 && R == 8)) {
                 C* wb = buf + fft16_pad(dst) * es;
 #pragma unroll
-                for (int r = 0; r < R; ++r) wb[(r * NS + ((r * NS) >> 4)) * es] = v[h + r * T];
+                for (int r = 0; r < R; ++r) {
+                    const int e = fft16_pad(dst) + r * NS + ((r * NS) >> 4);
+                    if (FCAS_CHECK(e == fft16_pad(dst + r * NS) && e < fft16_buf_elems(LOG_L), kCheckExchangeWrite))
+                        wb[(r * NS + ((r * NS) >> 4)) * es] = v[h + r * T];
+                }
             } else {
 #pragma unroll
-                for (int r = 0; r < R; ++r) buf[fft16_pad(dst + r * NS) * es] = v[h + r * T];
+                for (int r = 0; r < R; ++r)
+                    if (FCAS_CHECK(fft16_pad(dst + r * NS) < fft16_buf_elems(LOG_L), kCheckExchangeWrite))
+                        buf[fft16_pad(dst + r * NS) * es] = v[h + r * T];
             }
         }
         __syncthreads();

@@ -247,7 +247,10 @@ pass_a_kernel(const cplx<Real>* __restrict__ y, const Basis<Real>* __restrict__ 
     Basis<Real> bq[sizeof(Real) == 4 ? VH : 1];
     if constexpr (sizeof(Real) == 4) {
 #pragma unroll
-        for (int q = 0; q < VH; ++q) bq[q] = bb[(int64_t)q * G * K1B];
+        for (int q = 0; q < VH; ++q)
+            if (FCAS_CHECK(((int64_t)blk * (L / 2) + j) * K1B + c + (int64_t)q * G * K1B < ((int64_t)L / 2 << log_n1),
+                           kCheckBasis))
+                bq[q] = bb[(int64_t)q * G * K1B];
     }
     const int kbase = k1 + n1 * j;
     const int kstep = n1 * G;
@@ -272,7 +275,11 @@ pass_a_kernel(const cplx<Real>* __restrict__ y, const Basis<Real>* __restrict__ 
         const Real w1 = sc.w1[i], w2 = sc.w2[i];
 #pragma unroll
         for (int q = 0; q < VH; ++q) {
-            const C t = cmul(yd[(int64_t)q * G * K1B], dph);
+            C yv = mkc((Real)0, (Real)0);
+            if (FCAS_CHECK(((col0 + i) * (L / 2) + j) * K1B + c + (int64_t)q * G * K1B <
+                               (int64_t)n_det * ((int64_t)L / 2 << log_n1), kCheckSpectrum))
+                yv = yd[(int64_t)q * G * K1B];
+            const C t = cmul(yv, dph);
             r1[q].x += w1 * t.x;
             r1[q].y += w1 * t.y;
             r2[q].x += w2 * t.x;
@@ -300,7 +307,11 @@ pass_a_kernel(const cplx<Real>* __restrict__ y, const Basis<Real>* __restrict__ 
                 s += frac_mul_ff(cfh[3], cfl[3], b.b13.x, b.b13.y);
                 cp = fast_phasor(s - rintf(s));
             } else {
-                cp = unit_phasor(chirp_frac(bb[(int64_t)q * G * K1B], *pp));
+                Basis<Real> b{};
+                if (FCAS_CHECK(((int64_t)blk * (L / 2) + j) * K1B + c + (int64_t)q * G * K1B <
+                                   ((int64_t)L / 2 << log_n1), kCheckBasis))
+                    b = bb[(int64_t)q * G * K1B];
+                cp = unit_phasor(chirp_frac(b, *pp));
             }
             r1[q] = cmul(r1[q], cp);
             r2[q] = cmul(r2[q], cp);
@@ -328,7 +339,9 @@ pass_a_kernel(const cplx<Real>* __restrict__ y, const Basis<Real>* __restrict__ 
 #pragma unroll
         for (int q = 0; q < V; ++q) {
             const int ta = j + q * G;
-            __stcs(orow + (int64_t)ta * n1, cmul(v[q], w));   // streamed: read back only by pass B
+            if (FCAS_CHECK((p * kSeries + a) * (int64_t)L * n1 + k1 + (int64_t)ta * n1 < np * kSeries * (int64_t)L * n1,
+                           kCheckInterWrite))
+                __stcs(orow + (int64_t)ta * n1, cmul(v[q], w));   // streamed: read back only by pass B
             if (q + 1 < V) w = cmul(w, step);
         }
     }
@@ -375,7 +388,10 @@ pass_b_kernel(const cplx<Real>* __restrict__ inter, const ParticleParams* __rest
         const C* row = inter + ((p * kSeries + a) * n2 + ta) * (int64_t)L;
         C v[V];
 #pragma unroll
-        for (int q = 0; q < V; ++q) v[q] = row[j + q * G];
+        for (int q = 0; q < V; ++q)
+            if (FCAS_CHECK(((p * kSeries + a) * n2 + ta) * (int64_t)L + j + q * G < (int64_t)gridDim.y * kSeries * n2 * L,
+                           kCheckInterRead))
+                v[q] = row[j + q * G];
         fft16<Real, +1, LOG_L>(v, smem + c * BUF, 1, j, stw);
 #pragma unroll
         for (int q = 0; q < V; ++q) g[q] += v[q].x * v[q].x + v[q].y * v[q].y;
@@ -626,6 +642,19 @@ __global__ void stage_table_kernel(int log_l, int maxrb, double2* t64, float2* t
     }
     t64[m] = val;
     t32[m] = make_float2((float)val.x, (float)val.y);
+}
+
+unsigned int take_index_checks(cudaStream_t s) {
+#ifdef FCAS_CHECKED
+    unsigned int h = 0, zero = 0;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return 0;
+    cudaMemcpyFromSymbol(&h, g_index_checks, sizeof(h));
+    cudaMemcpyToSymbol(g_index_checks, &zero, sizeof(zero));
+    return h;
+#else
+    (void)s;
+    return 0;
+#endif
 }
 
 cudaError_t launch_stage_tables(int log_l, int maxrb, double2* t64, float2* t32, cudaStream_t s) {

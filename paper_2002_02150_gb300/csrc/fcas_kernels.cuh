@@ -92,6 +92,9 @@ cudaError_t launch_reduce(const Partial* partials, int64_t nb, const ParticlePar
                           int64_t np, double* fitness, int64_t* tc, cudaStream_t s);
 
 int pass_b_blocks_per_particle(int log_n1, int log_n2, int precision);
+// Checked build (FCAS_CHECKED): waits for the stream, returns and clears the bits of the index
+// checks that failed since the last call (see fcas_fft16.cuh). Other builds: 0, no synchronisation.
+unsigned int take_index_checks(cudaStream_t s);
 int pass_a_k1b_for(int log_n2, int precision);
 // compiled pass-A column-block widths for a length: writes up to 3 values, returns the count
 int pass_a_k1b_variants(int log_n2, int precision, int* out);

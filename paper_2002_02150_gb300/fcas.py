@@ -12,7 +12,8 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libfcas.so")
+# FCAS_LIBRARY selects another build of the same library (the index-checked build of the tests)
+LIB_PATH = os.environ.get("FCAS_LIBRARY") or os.path.join(_HERE, "libfcas.so")
 
 FCAS_MAX_DET = 8
 FCAS_PREC_FP64 = 0
