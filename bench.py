@@ -15,6 +15,7 @@ import argparse
 import dataclasses
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -159,6 +160,21 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
+# FP32 issue peak of the GB300 from the unit counts and the maximum SM clock: 152 SMs x 128 FP32
+# lanes x 2 flops (fused multiply-add) x 2.07 GHz; binary64 at the nominal 1.25 TFLOP/s.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP64_NOMINAL_TFLOPS = 1.25
+
+
+def flop_per_eval(n_fft, n_det, n_band):
+    """Algorithmic flops of one evaluation: two complex transforms of length N (5 N log2 N each), the
+    spectrum formation per band bin (per detector a complex product with the delay phasor and the
+    two weighted accumulations, 14 flops; then the chirp phase, 8, and two complex products, 12),
+    the inter-pass twiddle (one complex product per point of both series) and |W_1|^2 + |W_2|^2."""
+    log_n = int(round(math.log2(n_fft)))
+    return 2 * 5 * n_fft * log_n + n_band * (14 * n_det + 20) + 2 * 6 * n_fft + 4 * n_fft
+
+
 def measured_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -295,8 +311,11 @@ def bench_ours(args, ranks):
         torch.cuda.synchronize(dev)
         s64 = t0.elapsed_time(t1) / 1e3
         v64, _ = aggregate(ranks, n * args.fp64_steps, s64)
+        tf64 = v64 * flop_per_eval(w.n_fft, info["n_det"], info["n_band"]) / 1e12
         fp64 = {"value": round(v64, 2), "unit": UNIT, "steps": args.fp64_steps,
-                "ms_per_step": round(1e3 * s64 / args.fp64_steps, 3), "dtype": "f64"}
+                "ms_per_step": round(1e3 * s64 / args.fp64_steps, 3), "dtype": "f64",
+                "alu": {"bound": "alu", "achieved": round(tf64, 4), "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                        "frac": round(tf64 / FP64_NOMINAL_TFLOPS, 4), "peak_source": "nominal binary64 rate"}}
         ctx64.close()
 
     search = None if args.no_search else bench_search(fc, ranks, data, w, dev)
@@ -314,7 +333,14 @@ def bench_ours(args, ranks):
                    "shape": {"split_bias": info["split_bias"], "k1b": info["k1b"], "sub": info["sub"],
                              "autotuned": info["tuned_ms_per_particle"] > 0},
                    "l2": "inputs larger than L2 (intermediate %.1f GB per step), no flush" % (n * info["inter_bytes"] / 1e9)},
-        "roofline": roofline, "kernels": kernels, "gpu_launches": gpu_launches, "e2e": e2e, "clocks": clock,
+        "roofline": roofline,
+        "alu_view": {"flop_per_eval": flop_per_eval(w.n_fft, d, nband),
+                     "achieved": round(value / ranks.world * flop_per_eval(w.n_fft, d, nband) / 1e12, 3),
+                     "peak": round(FP32_PEAK_TFLOPS, 2), "unit": "TFLOP/s",
+                     "frac": round(value / ranks.world * flop_per_eval(w.n_fft, d, nband) / 1e12 / FP32_PEAK_TFLOPS, 4),
+                     "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                     "note": "whole fitness path per GPU; both passes issue-bound (see profiles/)"},
+        "kernels": kernels, "gpu_launches": gpu_launches, "e2e": e2e, "clocks": clock,
         "fp64_form": fp64, "cufft_form": cufft,
         "search_time_over_data_time": (search["search_time_over_data_time"] if search else
                                        {"value": round(PSO_EVALS / value / DATA_SECONDS, 5),
