@@ -292,8 +292,9 @@ def bench_ours(args, ranks):
 
     cufft = None
     if args.cufft_batches > 0:
-        cufft = bench_cufft(w, data, theta, fit.double().cpu().numpy(), tc.cpu().numpy(), dev,
-                            steps=args.cufft_batches)
+        ref = (fit.double().cpu().numpy(), tc.cpu().numpy())
+        cufft = bench_cufft(w, data, theta, *ref, dev, steps=args.cufft_batches)
+        cufft["fp64"] = bench_cufft(w, data, theta, *ref, dev, steps=args.cufft_batches, fp64=True)
 
     # plain binary64 form on the same workload (fewer steps: it is binary64-ALU bound)
     fp64 = None
@@ -368,14 +369,16 @@ def _chirp_coefficients(tau0, tau15, f_star):
     return 0.6 * f_star * tau0, f_star * tau1, -1.5 * f_star * tau15, 3.0 * f_star * tau2
 
 
-def bench_cufft(w, data, theta, fit_ref, tc_ref, dev, batch=4, steps=2):
+def bench_cufft(w, data, theta, fit_ref, tc_ref, dev, batch=4, steps=2, fp64=False):
     """The straightforward GPU form, timed for comparison: per particle and detector the spectrum
     Q_i[k] = 4 df y~^i[k] e^{2 pi i f_k Delta^i} h~_c*[k] is formed by PyTorch element-wise kernels
-    (binary64 phase, complex64 product), transformed by cuFFT (torch.fft.ifft, complex64, length N,
+    (binary64 phase, complex64 product; complex128 throughout with fp64), transformed by cuFFT
+    (torch.fft.ifft, complex64 or complex128, length N,
     one transform per detector), then projected, Gamma^2(t) = X_c^T G^-1 X_c + X_s^T G^-1 X_s, and
     maximised over t, each a separate kernel (the projection through the Cholesky factor of G^-1,
     as a sum of squares). Its results are compared with the fused path's."""
     import torch
+    cdt, rdt = (torch.complex128, torch.float64) if fp64 else (torch.complex64, torch.float32)
     d9 = np.asarray(data["det"], dtype=np.float64)
     n_det, n, fs = d9.shape[0], w.n_fft, w.fs
     df = fs / n
@@ -418,11 +421,11 @@ def bench_cufft(w, data, theta, fit_ref, tc_ref, dev, batch=4, steps=2):
         geo = [geometry(th) for th in ths]
         coef = torch.tensor([_chirp_coefficients(th[2], th[3], w.f_low) for th in ths], device=dev)
         delay = torch.tensor(np.stack([g[0] for g in geo]), device=dev)
-        wts = torch.tensor(np.stack([g[1] for g in geo]), device=dev, dtype=torch.float32)
+        wts = torch.tensor(np.stack([g[1] for g in geo]), device=dev, dtype=rdt)
         turns = (coef @ powers)[:, None, :] + delay[:, :, None] * f[None, None, :]
         turns = turns - torch.round(turns)
-        q = (ybase[None] * torch.polar(torch.ones_like(turns), 2.0 * np.pi * turns)).to(torch.complex64)
-        full = torch.zeros(b, n_det, n, dtype=torch.complex64, device=dev)
+        q = (ybase[None] * torch.polar(torch.ones_like(turns), 2.0 * np.pi * turns)).to(cdt)
+        full = torch.zeros(b, n_det, n, dtype=cdt, device=dev)
         full[:, :, sel] = q
         del q, turns
         z = torch.fft.ifft(full, dim=-1) * n
@@ -457,8 +460,9 @@ def bench_cufft(w, data, theta, fit_ref, tc_ref, dev, batch=4, steps=2):
     same_tc = float(np.mean(idx == np.asarray(tc_ref)[[j % len(theta) for j in range(m)]]))
     return {"value": round(m / sec, 2), "unit": UNIT, "particles": m,
             "max_rel_diff_vs_fused": rel, "same_tc_fraction": same_tc,
-            "how": "torch element-wise kernels (binary64 phase) + cuFFT complex64 inverse transforms of length N "
-                   "per detector + einsum projection + max, %d particles per batch" % batch}
+            "how": "torch element-wise kernels (binary64 phase) + cuFFT %s inverse transforms of length N "
+                   "per detector + einsum projection + max, %d particles per batch"
+                   % ("complex128" if fp64 else "complex64", batch)}
 
 
 def _pso_box(w):
