@@ -350,7 +350,7 @@ def bench_ours(args, ranks):
         "batched_uneven": group, "background_time_slides": background, "tiled_search": tiled,
         "paper_context": {"search_over_data": [1.4, 0.5], "hardware": "1 KNL node per PSO run, FP64"},
     }
-    if ranks.rank == 0 and args.cpu_sample > 0:
+    if ranks.rank == 0 and ranks.world == 1 and args.cpu_sample > 0:      # the CPU baseline is an N = 1 figure
         out["cpu_baseline"] = cpu_baseline(w, ranks.rank, theta, args.cpu_sample)
     return out
 
