@@ -299,6 +299,7 @@ def bench_ours(args, ranks):
     # plain binary64 form on the same workload (fewer steps: it is binary64-ALU bound)
     fp64 = None
     if args.fp64_steps > 0:
+        fit32, tc32 = fit.clone(), tc.clone()          # FP32-form results of the timed steps
         ctx64 = fc.fcas_create(data["det"], data["psd"], data["data"], w.n_fft, w.fs, w.f_low, w.f_high,
                                precision="fp64", max_batch=args.max_batch)
         for _ in range(1):
@@ -317,6 +318,11 @@ def bench_ours(args, ranks):
                 "ms_per_step": round(1e3 * s64 / args.fp64_steps, 3), "dtype": "f64",
                 "alu": {"bound": "alu", "achieved": round(tf64, 4), "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
                         "frac": round(tf64 / FP64_NOMINAL_TFLOPS, 4), "peak_source": "nominal binary64 rate"}}
+        # error of the FP32 form (float-float phase) against the binary64 form on the same particles
+        rel = ((fit32 - fit).abs() / fit.abs()).double().cpu().numpy()
+        fp64["fp32_form_error"] = {"max_rel": float(rel.max()), "median_rel": float(np.median(rel)),
+                                   "same_tc_fraction": float((tc32 == tc).double().mean().item()),
+                                   "particles": n}
         ctx64.close()
 
     search = None if args.no_search else bench_search(fc, ranks, data, w, dev)
