@@ -109,3 +109,24 @@ def test_group_search_equals_individual_searches():
                                                 box=box))
         assert got[s] == ref
         ctx.close()
+
+
+def test_group_of_mixed_precisions_equals_individual_searches():
+    import paper_2002_02150_gb300 as fc
+    base = sd.SMALL
+    segs = [(base, "fp32"), (base, "fp64"), (dataclasses.replace(base, n_fft=8192, n_samples=6000), "fp64")]
+    t0lo, t0hi, t15lo, t15hi = sd.chirp_time_box(base.f_low)
+    box = (0.0, 2 * math.pi, -0.5 * math.pi, 0.5 * math.pi, t0lo, t0hi, t15lo, t15hi)
+    cfg = fc.pso_config(n_runs=2, n_particles=8, n_iter=12, seed=11, box=box)
+    ctxs = []
+    for s, (w, prec) in enumerate(segs):
+        d = sd.make_dataset(w, 40 + s)
+        ctxs.append(fc.fcas_create(d["det"], d["psd"], d["data"], w.n_fft, w.fs, w.f_low, w.f_high, precision=prec,
+                                   flags=fc.FCAS_SETUP_LAZY_SCRATCH))
+    with fc.fcas_group_create(ctxs, max_batch=5) as grp:
+        got = grp.search(cfg)
+    for s, ctx in enumerate(ctxs):
+        ref = fc.fcas_search(ctx, fc.pso_config(n_runs=2, n_particles=8, n_iter=12, seed=fc.segment_seed(11, s),
+                                                box=box))
+        assert got[s] == ref
+        ctx.close()
