@@ -17,6 +17,7 @@ import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -152,11 +153,19 @@ FITNESS_KERNEL_SOURCES = ["paper_2002_02150_gb300/csrc/fcas_kernels.cu", "paper_
                           "include/fcas.h"]
 
 
+def _code_only(text):
+    """C/C++ source without comments and with whitespace collapsed (edits to comments do not change
+    the kernels)."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_source_hash():
-    """Hash of the files the fitness kernels (pass A, pass B) are compiled from."""
+    """Hash of the code (comments excluded) the fitness kernels (pass A, pass B) are compiled from."""
     h = hashlib.sha256()
     for p in FITNESS_KERNEL_SOURCES:
-        h.update(open(os.path.join(ROOT, p), "rb").read())
+        h.update(_code_only(open(os.path.join(ROOT, p)).read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -289,7 +289,7 @@ void fcas_group_destroy(fcas_group* group);
 
 /*
  * fcas_tau_tiles -- n0 x n15 overlapping rectangles covering [tau0_lo, tau0_hi] x [tau15_lo, tau15_hi]
- * (Sec. IV: a set of rectangles with an overlap fraction covers the chirp-time range). Along each
+ * (Sec. IV covers the chirp-time range with overlapping rectangles searched in parallel). Along each
  * axis the n tiles have width w = (hi - lo) / (n - (n - 1) overlap) and tile j starts at
  * lo + j (1 - overlap) w, so neighbours share the fraction `overlap` of a width and the last tile
  * ends at hi. Written as PSO boxes over the whole sky (alpha in [0, 2 pi], delta in [-pi/2, pi/2])
