@@ -352,12 +352,14 @@ pass_a_kernel(const cplx<Real>* __restrict__ y, const Basis<Real>* __restrict__ 
 // |W2(t)|^2 for t = ta + N2 tb (Sec. II.C, the maximisation over A_k in closed form), and the
 // argmax over the CTA's rows (lowest t on ties).
 // ------------------------------------------------------------------------------------------
-__device__ __forceinline__ bool better_f(float v, int t, float bv, int bt) {
-    return v > bv || (v == bv && t < bt);
+// Resident pass-B CTAs per SM the compiler is held to: three for the FP32 form's 2^11- and
+// 2^12-point rows (76-77 registers, no spills), two for other CTAs of up to 256 threads.
+__host__ __device__ constexpr int pass_b_min_blocks(int log_l, int real_bytes) {
+    return pass_b_threads(log_l, real_bytes) > 256 ? 1 : (real_bytes == 4 && (log_l == 11 || log_l == 12)) ? 3 : 2;
 }
 
 template <typename Real, int LOG_L>
-__global__ void __launch_bounds__(pass_b_threads(LOG_L, sizeof(Real)), pass_b_threads(LOG_L, sizeof(Real)) <= 256 ? 2 : 1)
+__global__ void __launch_bounds__(pass_b_threads(LOG_L, sizeof(Real)), pass_b_min_blocks(LOG_L, sizeof(Real)))
 pass_b_kernel(const cplx<Real>* __restrict__ inter, const ParticleParams* __restrict__ params, int64_t p0,
               int log_n2, int64_t n_samples, const cplx<Real>* __restrict__ stw, Partial* __restrict__ partials) {
     using C = cplx<Real>;
@@ -396,12 +398,13 @@ pass_b_kernel(const cplx<Real>* __restrict__ inter, const ParticleParams* __rest
 #pragma unroll
         for (int q = 0; q < V; ++q) g[q] += v[q].x * v[q].x + v[q].y * v[q].y;
     }
+    // t = ta + N2 (j + q G) grows with q, so a strict comparison keeps the lowest t among equal values
     Real best = (Real)-1;
     int bt = INT_MAX;
 #pragma unroll
     for (int q = 0; q < V; ++q) {
         const int t = ta + n2 * (j + q * G);
-        if (t < n_samples && (g[q] > best || (g[q] == best && t < bt))) {
+        if (t < n_samples && g[q] > best) {
             best = g[q];
             bt = t;
         }
