@@ -185,3 +185,30 @@ def test_largest_supported_length_sampled():
         fit, tc = gpu_fitness(ctx, theta)
     assert np.all(np.isfinite(fit)) and np.all((tc >= 0) & (tc < w.n_samples))
     assert_parity(oracle_setup(w, data), theta[:2], fit[:2], tc[:2], "fp32", "N=2^24")
+
+
+def test_two_contexts_on_two_streams_match_sequential_results():
+    """Contexts hold no shared state: calls on two streams overlapping on the GPU give the results
+    of the same calls made one after the other."""
+    import torch
+    import paper_2002_02150_gb300 as fc
+    w = sd.C1
+    d1, d2 = sd.make_dataset(w, 51), sd.make_dataset(w, 52)
+    th = torch.tensor(sd.make_particles(w, 96, seed=51), device="cuda:0")
+    with make_ctx(w, d1, "fp32") as c1, make_ctx(w, d2, "fp32") as c2:
+        ref1 = [x.clone() for x in fc.fcas_fitness(c1, th)]
+        ref2 = [x.clone() for x in fc.fcas_fitness(c2, th)]
+        torch.cuda.synchronize()
+        s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+        outs = []
+        for _ in range(4):
+            f1 = torch.empty(96, dtype=torch.float64, device="cuda:0")
+            t1 = torch.empty(96, dtype=torch.int64, device="cuda:0")
+            f2, t2 = torch.empty_like(f1), torch.empty_like(t1)
+            fc.fcas_fitness(c1, th, f1, t1, stream=s1.cuda_stream)
+            fc.fcas_fitness(c2, th, f2, t2, stream=s2.cuda_stream)
+            outs.append((f1, t1, f2, t2))
+        torch.cuda.synchronize()
+    for f1, t1, f2, t2 in outs:
+        assert torch.equal(f1, ref1[0]) and torch.equal(t1, ref1[1])
+        assert torch.equal(f2, ref2[0]) and torch.equal(t2, ref2[1])
