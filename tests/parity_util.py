@@ -3,7 +3,6 @@ seeded inputs and compare fitness and argmax element by element."""
 
 import numpy as np
 
-import synthdata as sd
 from oracle import fcas_oracle as o
 
 # Parity tolerance of the FP32 form (float-float phase): |Gamma^2_GPU - Gamma^2_oracle| / Gamma^2_oracle

@@ -1,8 +1,6 @@
 """GPU adjoint gradient of the coherent fitness at fixed t_c against the oracle's FP64 gradient
 (complex step) and central finite differences; the torch.autograd path; gradient polishing."""
 
-import dataclasses
-
 import numpy as np
 import pytest
 
