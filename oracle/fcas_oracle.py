@@ -127,6 +127,15 @@ def antenna_patterns(det, alpha, delta, psi=0.0):
     return out
 
 
+def condition_number(det, alpha, delta):
+    """Condition number of the antenna-pattern matrix F(alpha, delta, psi) (Sec. V: the ill-posedness
+    of the network problem at a sky position): the ratio of the largest to the smallest singular
+    value of the (D, 2) matrix, by the singular value decomposition. It does not depend on psi,
+    which only rotates the columns; +inf when F has rank one."""
+    s = np.linalg.svd(antenna_patterns(det, alpha, delta, 0.0), compute_uv=False)
+    return float(s[0] / s[1]) if len(s) > 1 and s[1] > 0.0 else math.inf   # D = 1: one singular value
+
+
 def arrival_delays(det, alpha, delta):
     """Delta^i = -n . r_i / c: the wave reaches detector i Delta^i after the ECEF origin."""
     n, _, _ = sky_vectors(alpha, delta)

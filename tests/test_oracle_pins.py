@@ -105,6 +105,33 @@ def test_antenna_patterns_polar_detector_closed_form(alpha, delta, psi):
     assert got @ got == pytest.approx(textbook(0.0) @ textbook(0.0), rel=1e-13)
 
 
+@pytest.mark.parametrize("alpha,delta", [(0.4, 1.5707963267948966), (1.1, 0.9), (3.0, 0.3), (5.2, -0.6), (2.2, 0.0)])
+def test_condition_number_of_a_colocated_45_degree_pair(alpha, delta):
+    """Two detectors at the north pole, the second with its arms turned by 45 degrees: at polar
+    angle th the columns of F are orthogonal with norms (1 + cos^2 th)/2 and |cos th|, so the
+    condition number is (1 + cos^2 th) / (2 |cos th|): 1 overhead, +inf in the arms' plane."""
+    r = math.sqrt(0.5)
+    det = np.array([[0, 0, 6.4e6, 1, 0, 0, 0, 1, 0],
+                    [0, 0, 6.4e6, r, r, 0, -r, r, 0]], dtype=float)
+    ct = math.cos(math.pi / 2 - delta)
+    got = o.condition_number(det, alpha, delta)
+    if abs(ct) < 1e-12:
+        assert got == math.inf or got > 1e12
+    else:
+        assert got == pytest.approx((1 + ct * ct) / (2 * abs(ct)), rel=1e-12)
+
+
+def test_condition_number_single_detector_and_psi_invariance():
+    det = sd.detector_geometry()
+    assert o.condition_number(det[:1], 1.0, 0.3) == math.inf          # one detector: rank one
+    rng = np.random.default_rng(9)
+    for _ in range(20):
+        a, d, psi = rng.uniform(0, 2 * math.pi), math.asin(rng.uniform(-1, 1)), rng.uniform(0, math.pi)
+        s = np.linalg.svd(o.antenna_patterns(det, a, d, psi), compute_uv=False)
+        k = o.condition_number(det, a, d)
+        assert k >= 1.0 and s[0] / s[1] == pytest.approx(k, rel=1e-12)
+
+
 def test_delays_bounded_by_baseline_and_tight_along_it():
     det = sd.detector_geometry()
     rng = np.random.default_rng(5)
