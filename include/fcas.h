@@ -214,6 +214,18 @@ int fcas_pso_update(const fcas_pso_config* cfg, int32_t iter, const double* fitn
 int fcas_pso_theta(const fcas_pso_config* cfg, const double* x, double* theta, void* stream);
 
 /*
+ * fcas_condition_number -- condition number of the antenna-pattern matrix F(alpha, delta, psi) of the
+ * context's network at each particle's sky position (Sec. V relates the ill-posedness of the network
+ * problem, and the splitting of the sky-error region, to it): the ratio of the largest to the
+ * smallest singular value of the D x 2 matrix, independent of psi.
+ *   theta : [n][4] particles (only alpha, delta are read) (host or device).
+ *   kappa : [n] condition numbers (host or device); +inf when F has rank one (one detector, or all
+ *           detectors seeing the same polarisation), NaN for a non-finite angle.
+ * Asynchronous when both arrays are on the device, synchronous otherwise.
+ */
+int fcas_condition_number(fcas_ctx* ctx, int64_t n, const double* theta, double* kappa, void* stream);
+
+/*
  * fcas_search -- the full search on the context's data: n_runs x n_particles particles evolve
  * together on the device for n_iter iterations; every iteration (positions -> parameters,
  * fitness, update) is one CUDA-graph launch with no host round trip. results: host array

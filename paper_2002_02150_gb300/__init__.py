@@ -5,10 +5,10 @@ from .fcas import (FcasError, Context, fcas_create, fcas_fitness, fcas_fitness_n
                    fcas_profile_enable, fcas_profile_read, load_library, LIB_PATH, pso_config, fcas_pso_init,
                    fcas_pso_update, fcas_search, fcas_gradient, coherent_fitness, polish, fcas_autotune,
                    fcas_set_shape, fcas_group_create, Group, segment_seed, FCAS_SETUP_LAZY_SCRATCH, pso_theta,
-                   fcas_tau_tiles, time_slide_background)
+                   fcas_tau_tiles, time_slide_background, fcas_condition_number)
 
 __all__ = ["FcasError", "Context", "fcas_create", "fcas_fitness", "fcas_fitness_noalloc", "fcas_destroy", "fcas_last_error",
            "fcas_get_info", "fcas_profile_enable", "fcas_profile_read", "load_library", "LIB_PATH", "pso_config",
            "fcas_pso_init", "fcas_pso_update", "fcas_search", "fcas_gradient", "coherent_fitness", "polish",
            "fcas_autotune", "fcas_set_shape", "fcas_group_create", "Group", "segment_seed", "FCAS_SETUP_LAZY_SCRATCH",
-           "pso_theta", "fcas_tau_tiles", "time_slide_background"]
+           "pso_theta", "fcas_tau_tiles", "time_slide_background", "fcas_condition_number"]

@@ -972,6 +972,32 @@ int fcas_gradient(fcas_ctx* c, int64_t n, const double* theta, const int64_t* tc
     return FCAS_OK;
 }
 
+int fcas_condition_number(fcas_ctx* c, int64_t n, const double* theta, double* kappa, void* stream) {
+    g_last_error.clear();
+    if (!c) return fail(FCAS_ERR_INVALID, "fcas_condition_number: NULL context");
+    if (n < 0) return fail(FCAS_ERR_INVALID, "fcas_condition_number: n < 0");
+    if (n == 0) return FCAS_OK;
+    if (!theta || !kappa) return fail(FCAS_ERR_INVALID, "fcas_condition_number: NULL array");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool th_dev = is_device_ptr(theta), k_dev = is_device_ptr(kappa);
+    if (!th_dev || !k_dev) {
+        const int rc = ensure_staging(c, n);
+        if (rc) return rc;
+    }
+    const double* d_theta = theta;
+    if (!th_dev) {
+        FCAS_CUDA(cudaMemcpyAsync(c->d_theta, theta, sizeof(double) * 4 * (size_t)n, cudaMemcpyHostToDevice, st));
+        d_theta = c->d_theta;
+    }
+    double* d_kappa = k_dev ? kappa : c->d_fit;
+    FCAS_CUDA(launch_condition(d_theta, n, c->d_det, c->setup.n_det, d_kappa, st));
+    if (!k_dev) {
+        FCAS_CUDA(cudaMemcpyAsync(kappa, d_kappa, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, st));
+        FCAS_CUDA(cudaStreamSynchronize(st));
+    }
+    return FCAS_OK;
+}
+
 void fcas_destroy(fcas_ctx* c) {
     if (!c) return;
     cudaDeviceSynchronize();

@@ -125,6 +125,8 @@ def load_library():
     lib.fcas_group_search_boxes.restype = i32
     lib.fcas_tau_tiles.argtypes = [dp, dp, dp, dp, ctypes.c_int32, ctypes.c_int32, dp, ctypes.POINTER(dp)]
     lib.fcas_tau_tiles.restype = i32
+    lib.fcas_condition_number.argtypes = [vp, i64, vp, vp, vp]
+    lib.fcas_condition_number.restype = i32
     _lib = lib
     return lib
 
@@ -508,3 +510,19 @@ def time_slide_background(det, psd, data, n_fft, fs, f_low, f_high, shifts, cfg,
             c.close()
     best = np.array([max(r["fitness"] for r in seg) for seg in res])
     return best, res
+
+
+def fcas_condition_number(ctx, theta, kappa=None, stream=None):
+    """Condition number of the antenna-pattern matrix at each particle's (alpha, delta) (C:
+    fcas_condition_number). Output defaults to the memory kind of theta."""
+    n = int(theta.shape[0]) if len(theta.shape) == 2 else int(np.prod(theta.shape)) // 4
+    if kappa is None:
+        if _is_torch(theta) and theta.is_cuda:
+            import torch
+            kappa = torch.empty(n, dtype=torch.float64, device=theta.device)
+        else:
+            kappa = np.empty(n, dtype=np.float64)
+    p_th, k1 = _ptr(theta, np.float64)
+    p_k, k2 = _ptr(kappa, np.float64)
+    _check(load_library().fcas_condition_number(ctx.handle, n, p_th, p_k, _stream(stream, theta, kappa)))
+    return kappa

@@ -212,3 +212,23 @@ def test_two_contexts_on_two_streams_match_sequential_results():
     for f1, t1, f2, t2 in outs:
         assert torch.equal(f1, ref1[0]) and torch.equal(t1, ref1[1])
         assert torch.equal(f2, ref2[0]) and torch.equal(t2, ref2[1])
+
+
+def test_condition_number_matches_the_oracle():
+    import torch
+    import paper_2002_02150_gb300 as fc
+    w = sd.SMALL
+    data = sd.make_dataset(w, 61)
+    theta = sd.make_particles(w, 200, seed=61)
+    theta[:2, :2] = [[math.radians(32.09), math.radians(-53.86)], [math.radians(150.11), math.radians(-60.16)]]
+    with make_ctx(w, data, "fp32") as ctx:
+        k_host = fc.fcas_condition_number(ctx, theta)
+        k_dev = fc.fcas_condition_number(ctx, torch.tensor(theta, device="cuda:0")).cpu().numpy()
+    ref = np.array([o.condition_number(np.asarray(data["det"]), th[0], th[1]) for th in theta])
+    np.testing.assert_allclose(k_host, ref, rtol=1e-10)
+    assert np.array_equal(k_host, k_dev)
+    # one detector: rank one everywhere
+    w1 = dataclasses.replace(sd.SMALL, detectors=("L1",))
+    d1 = sd.make_dataset(w1, 62)
+    with make_ctx(w1, d1, "fp64") as ctx1:
+        assert np.all(np.isinf(fc.fcas_condition_number(ctx1, theta[:10])))
