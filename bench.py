@@ -162,10 +162,14 @@ def _code_only(text):
 
 
 def kernel_source_hash():
-    """Hash of the code (comments excluded) the fitness kernels (pass A, pass B) are compiled from."""
+    """Hash of the code (comments excluded) the fitness kernels (pass A, pass B) are compiled from;
+    of the public header only its macros (declarations of other entry points do not change them)."""
     h = hashlib.sha256()
     for p in FITNESS_KERNEL_SOURCES:
-        h.update(_code_only(open(os.path.join(ROOT, p)).read()).encode())
+        text = _code_only(open(os.path.join(ROOT, p)).read())
+        if p.endswith("fcas.h"):
+            text = " ".join(ln for ln in open(os.path.join(ROOT, p)).read().splitlines() if ln.startswith("#define"))
+        h.update(text.encode())
     return h.hexdigest()[:16]
 
 

@@ -11,6 +11,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include "fcas_ctx.cuh"
+#include "fcas_diag.cuh"
 #include "fcas_kernels.cuh"
 #include "fcas_pso.cuh"
 

@@ -75,9 +75,6 @@ struct FitnessPlan {
 };
 
 // Per-particle geometry (binary64): chirp coefficients, delays, antenna patterns, G^-1.
-// Condition number of the antenna-pattern matrix per particle (+inf for rank one, NaN for a non-finite angle).
-cudaError_t launch_condition(const double* theta, int64_t n, const double* det9, int n_det, double* kappa,
-                             cudaStream_t s);
 cudaError_t launch_geometry(const double* theta, int64_t n, ParticleParams* out, const double* det9,
                             const double* sigma2_scaled, int n_det, double f_star, double df,
                             cudaStream_t s);
