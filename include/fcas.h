@@ -219,8 +219,9 @@ int fcas_pso_theta(const fcas_pso_config* cfg, const double* x, double* theta, v
  * problem, and the splitting of the sky-error region, to it): the ratio of the largest to the
  * smallest singular value of the D x 2 matrix, independent of psi.
  *   theta : [n][4] particles (only alpha, delta are read) (host or device).
- *   kappa : [n] condition numbers (host or device); +inf when F has rank one (one detector, or all
- *           detectors seeing the same polarisation), NaN for a non-finite angle.
+ *   kappa : [n] condition numbers (host or device); +inf when F is numerically of rank one
+ *           (det(F^T F) < 1e-12 (tr(F^T F)/2)^2, the rule the projection uses for G: one detector, or
+ *           all detectors seeing the same polarisation), NaN for a non-finite angle.
  * Asynchronous when both arrays are on the device, synchronous otherwise.
  */
 int fcas_condition_number(fcas_ctx* ctx, int64_t n, const double* theta, double* kappa, void* stream);

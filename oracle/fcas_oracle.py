@@ -131,9 +131,14 @@ def condition_number(det, alpha, delta):
     """Condition number of the antenna-pattern matrix F(alpha, delta, psi) (Sec. V: the ill-posedness
     of the network problem at a sky position): the ratio of the largest to the smallest singular
     value of the (D, 2) matrix, by the singular value decomposition. It does not depend on psi,
-    which only rotates the columns; +inf when F has rank one."""
-    s = np.linalg.svd(antenna_patterns(det, alpha, delta, 0.0), compute_uv=False)
-    return float(s[0] / s[1]) if len(s) > 1 and s[1] > 0.0 else math.inf   # D = 1: one singular value
+    which only rotates the columns; +inf when F is (numerically) of rank one, by the rule used for
+    G: det(F^T F) < RANK1_RTOL (tr(F^T F) / 2)^2."""
+    f = antenna_patterns(det, alpha, delta, 0.0)
+    g = f.T @ f
+    if g[0, 0] * g[1, 1] - g[0, 1] * g[1, 0] < RANK1_RTOL * (0.5 * (g[0, 0] + g[1, 1])) ** 2:
+        return math.inf
+    s = np.linalg.svd(f, compute_uv=False)
+    return float(s[0] / s[1])
 
 
 def arrival_delays(det, alpha, delta):

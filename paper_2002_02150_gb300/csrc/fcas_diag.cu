@@ -35,9 +35,13 @@ __global__ void condition_kernel(const double* __restrict__ theta, int64_t n, co
         b += fp * fx;
         c += fx * fx;
     }
-    const double hi = 0.5 * (a + c) + sqrt(0.25 * (a - c) * (a - c) + b * b);
-    const double lo = hi > 0.0 ? (a * c - b * b) / hi : 0.0;     // product / larger: no cancellation
-    kappa[p] = lo > 0.0 ? sqrt(hi / lo) : __longlong_as_double(0x7ff0000000000000LL);
+    const double det = a * c - b * b, tr = a + c;
+    if (det < kRank1Rtol * (0.5 * tr) * (0.5 * tr)) {     // numerically rank one (the rule used for G)
+        kappa[p] = __longlong_as_double(0x7ff0000000000000LL);
+        return;
+    }
+    const double hi = 0.5 * tr + sqrt(0.25 * (a - c) * (a - c) + b * b);
+    kappa[p] = sqrt(hi / (det / hi));                      // larger / smaller eigenvalue of F^T F
 }
 
 cudaError_t launch_condition(const double* theta, int64_t n, const double* det9, int n_det, double* kappa,
