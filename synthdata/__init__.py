@@ -9,10 +9,11 @@ projection, no argmax) and imports neither ``oracle`` nor the CUDA package.
 
 from .sites import SITES, detector_geometry
 from .psd import aligo_fit_psd, psd_on_grid
-from .workloads import Workload, SMALL, C1, C2, workload_by_name, make_dataset, make_particles, chirp_time_box
+from .workloads import (Workload, SMALL, C1, C2, PAPER_DNS, PAPER_TAU_BOX, workload_by_name, make_dataset,
+                        make_particles, chirp_time_box)
 
 __all__ = [
     "SITES", "detector_geometry", "aligo_fit_psd", "psd_on_grid",
-    "Workload", "SMALL", "C1", "C2", "workload_by_name", "make_dataset", "make_particles",
-    "chirp_time_box",
+    "Workload", "SMALL", "C1", "C2", "PAPER_DNS", "PAPER_TAU_BOX", "workload_by_name", "make_dataset",
+    "make_particles", "chirp_time_box",
 ]

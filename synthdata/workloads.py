@@ -59,7 +59,14 @@ C1 = Workload("4det-64s-1024Hz", fs=1024.0, n_samples=65536, n_fft=65536, f_low=
 C2 = Workload("4det-60min-2048Hz", fs=2048.0, n_samples=7372800, n_fft=1 << 23, f_low=30.0, f_high=1000.0,
               m1=1.4, m2=1.4, snr=10.0, arrival_s=1200.0, n_particles=320)
 
-_BY_NAME = {w.name: w for w in (SMALL, C1, C2)}
+# The paper's own search configuration (Sec. V): 4 det x 60 min @ 2048 Hz with f_* = 10 Hz, an
+# equal-mass 1.5 + 1.5 Msun signal arriving 20 min into the data (it lasts 15.1 min from 10 Hz),
+# searched over tau0 in [500, 1500] s, tau1.5 in [5, 15] s; SNR 12.
+PAPER_DNS = Workload("4det-60min-2048Hz-fstar10", fs=2048.0, n_samples=7372800, n_fft=1 << 23, f_low=10.0,
+                     f_high=1000.0, m1=1.5, m2=1.5, snr=12.0, arrival_s=1200.0, n_particles=40)
+PAPER_TAU_BOX = (500.0, 1500.0, 5.0, 15.0)
+
+_BY_NAME = {w.name: w for w in (SMALL, C1, C2, PAPER_DNS)}
 
 
 def workload_by_name(name):

@@ -232,3 +232,18 @@ def test_condition_number_matches_the_oracle():
     d1 = sd.make_dataset(w1, 62)
     with make_ctx(w1, d1, "fp64") as ctx1:
         assert np.all(np.isinf(fc.fcas_condition_number(ctx1, theta[:10])))
+
+
+@pytest.mark.parametrize("precision", FORMS)
+def test_paper_chirp_time_box_at_f_star_10hz(precision):
+    """The paper's search box at f_* = 10 Hz (Sec. V: tau0 up to 1500 s, chirp phases of up to
+    ~10^4 turns at the low-frequency end), on a 512-s segment at 512 Hz, band 10-200 Hz."""
+    w = dataclasses.replace(sd.PAPER_DNS, fs=512.0, n_samples=250000, n_fft=1 << 18, f_high=200.0, arrival_s=20.0)
+    data = sd.make_dataset(w, 71)
+    lo0, hi0, lo15, hi15 = sd.PAPER_TAU_BOX
+    rng = np.random.default_rng(71)
+    theta = np.stack([rng.uniform(0, 2 * math.pi, 6), np.arcsin(rng.uniform(-1, 1, 6)),
+                      rng.uniform(lo0, hi0, 6), rng.uniform(lo15, hi15, 6)], axis=1)
+    with make_ctx(w, data, precision) as ctx:
+        fit, tc = gpu_fitness(ctx, theta)
+    assert_parity(oracle_setup(w, data), theta, fit, tc, precision, "f*=10Hz")
