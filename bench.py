@@ -620,7 +620,9 @@ def bench_paper_config(fc, ranks, dev, n_iter):
     if ranks.rank == 0:
         setup = o.OracleSetup(data["det"], data["psd"], data["data"], w.n_fft, w.fs, w.f_low, w.f_high)
         g_ref, t_ref = o.fitness(setup, best["theta"])
-        out.update({"oracle_fitness_at_best": g_ref, "rel_diff": abs(best["fitness"] - g_ref) / g_ref})
+        g_true, t_true = o.fitness(setup, [inj["alpha"], inj["delta"], t0, t15])
+        out.update({"oracle_fitness_at_best": g_ref, "rel_diff": abs(best["fitness"] - g_ref) / g_ref,
+                    "oracle_fitness_at_injection": g_true, "oracle_tc_s_at_injection": t_true / w.fs})
     return out
 
 
