@@ -113,3 +113,16 @@ def test_polish_improves_pso_best_particles_judged_by_the_oracle():
         th2, after, acc = fc.polish(ctx, theta, steps=10, judge=judge)
     assert np.all(after >= before)
     assert np.any(after > before)
+
+
+def test_gradient_60min_sampled():
+    """The 60-min workload (N = 2^23): the adjoint gradient of two particles in both forms against
+    the oracle's complex-step gradient at the same t_c."""
+    w = sd.C2
+    data = sd.make_dataset(w, 0)
+    theta = sd.make_particles(w, 2, seed=5)
+    setup = oracle_setup(w, data)
+    for precision in ("fp32", "fp64"):
+        with make_ctx(w, data, precision) as ctx:
+            f, tc, g = _gpu_grad(ctx, theta)
+        _check(setup, theta, tc, g, precision, f"60min {precision}")
