@@ -150,7 +150,7 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------------------- roofline
-FITNESS_KERNEL_SOURCES = ["paper_2002_02150_gb300/csrc/fcas_kernels.cu", "paper_2002_02150_gb300/csrc/fcas_kernels.cuh",
+FITNESS_KERNEL_SOURCES = ["paper_2002_02150_gb300/csrc/fcas_passes.cuh", "paper_2002_02150_gb300/csrc/fcas_kernels.cuh",
                           "paper_2002_02150_gb300/csrc/fcas_fft16.cuh", "paper_2002_02150_gb300/csrc/fcas_internal.cuh",
                           "include/fcas.h"]
 

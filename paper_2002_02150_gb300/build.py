@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfcas.so")
 SOURCES = ["fcas_api.cu", "fcas_kernels.cu", "fcas_create.cu", "fcas_noalloc.cu", "fcas_pso.cu", "fcas_grad.cu",
-           "fcas_diag.cu"]
+           "fcas_diag.cu", "fcas_kernels_ff.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

@@ -72,6 +72,7 @@ namespace {
 void free_ctx(fcas_ctx* c) {
     void* ptrs[] = {c->d_det, c->d_sigma2s, c->d_y, c->d_basis, c->d_tw64, c->d_twlo64, c->d_twhi64,
                     c->d_tw32, c->d_twlo32, c->d_twhi32, c->d_stw_a64, c->d_stw_a32, c->d_stw_b64, c->d_stw_b32,
+                    c->d_twloff, c->d_twhiff, c->d_stw_aff, c->d_stw_bff,
                     c->d_params, c->d_theta, c->d_fit, c->d_tc, c->d_inter, c->d_partials, c->d_pso,
                     c->d_gsums, c->d_gstage, c->d_ynat};
     for (void* p : ptrs)
@@ -156,19 +157,17 @@ void prof_end(fcas_ctx* c, size_t slot, cudaStream_t s) {
 cudaError_t launch_passes_with(fcas_ctx* c, const ParticleParams* params, void* inter, Partial* partials,
                                int64_t chunk, int64_t n, double* d_fit, int64_t* d_tc, cudaStream_t st) {
     const FitnessPlan plan = make_plan(c);
-    const bool fp32 = c->setup.precision == FCAS_PREC_FP32;
+    const int prec = c->setup.precision;
     size_t slot;
     cudaError_t e = cudaSuccess;
     for (int64_t p0 = 0; p0 < n && e == cudaSuccess; p0 += chunk) {
         const int64_t np = (n - p0) < chunk ? (n - p0) : chunk;
         prof_begin(c, FCAS_KERNEL_PASS_A, st, &slot);
-        e = fp32 ? launch_pass_a<float>(plan, params, p0, np, inter, st)
-                 : launch_pass_a<double>(plan, params, p0, np, inter, st);
+        e = launch_pass_a_prec(prec, plan, params, p0, np, inter, st);
         prof_end(c, slot, st);
         if (e != cudaSuccess) break;
         prof_begin(c, FCAS_KERNEL_PASS_B, st, &slot);
-        e = fp32 ? launch_pass_b<float>(plan, params, p0, np, inter, partials, st)
-                 : launch_pass_b<double>(plan, params, p0, np, inter, partials, st);
+        e = launch_pass_b_prec(prec, plan, params, p0, np, inter, partials, st);
         prof_end(c, slot, st);
         if (e != cudaSuccess) break;
         prof_begin(c, FCAS_KERNEL_REDUCE, st, &slot);
@@ -221,6 +220,8 @@ int apply_layout(fcas_ctx* c, int bias, int k1b, int sub, int radix_bits_a, cuda
     c->nb_partials = nb;
     cudaError_t e = launch_stage_tables(l2, radix_bits_a, c->d_stw_a64, c->d_stw_a32, st);
     if (e == cudaSuccess) e = launch_stage_tables(l1, 4, c->d_stw_b64, c->d_stw_b32, st);
+    if (e == cudaSuccess && c->d_stw_aff) e = launch_split_ff(c->d_stw_a64, c->d_stw_aff, (int64_t)1 << l2, st);
+    if (e == cudaSuccess && c->d_stw_bff) e = launch_split_ff(c->d_stw_b64, c->d_stw_bff, (int64_t)1 << l1, st);
     if (e == cudaSuccess)
         e = launch_layout(c->d_ynat, c->setup.n_det, log_n, l1, l2, k1b, c->k_lo, c->k_hi, c->setup.fs, c->setup.f_low,
                           c->setup.precision, c->d_y, c->d_basis, st);
@@ -267,8 +268,9 @@ int create_impl(fcas_ctx** out, const fcas_setup* setup, const fcas_detector* de
     const fcas_setup& s = *setup;
     if (s.n_det < 1 || s.n_det > FCAS_MAX_DET)
         return fail(FCAS_ERR_INVALID, "n_det = %d outside 1..%d", s.n_det, FCAS_MAX_DET);
-    if (s.precision != FCAS_PREC_FP32 && s.precision != FCAS_PREC_FP64)
-        return fail(FCAS_ERR_INVALID, "precision = %d is not FCAS_PREC_FP32 or FCAS_PREC_FP64", s.precision);
+    if (s.precision != FCAS_PREC_FP32 && s.precision != FCAS_PREC_FP64 && s.precision != FCAS_PREC_FF)
+        return fail(FCAS_ERR_INVALID, "precision = %d is not FCAS_PREC_FP32, FCAS_PREC_FP64 or FCAS_PREC_FF",
+                    s.precision);
     const int log_n = ilog2_exact(s.n_fft);
     if (log_n < kMinLogN || log_n > kMaxLogN)
         return fail(FCAS_ERR_INVALID, "n_fft = %lld is not a power of two in 2^%d..2^%d", (long long)s.n_fft, kMinLogN,
@@ -417,6 +419,14 @@ int create_impl(fcas_ctx** out, const fcas_setup* setup, const fcas_detector* de
     c->d_tw = fp32 ? (void*)c->d_tw32 : (void*)c->d_tw64;
     c->d_twlo = fp32 ? (void*)c->d_twlo32 : (void*)c->d_twlo64;
     c->d_twhi = fp32 ? (void*)c->d_twhi32 : (void*)c->d_twhi64;
+    if (s.precision == FCAS_PREC_FF) {
+        FCAS_TRY(dev_alloc(&c->d_twloff, sizeof(double2) * nlo, "float-float twiddles"));
+        FCAS_TRY(dev_alloc(&c->d_twhiff, sizeof(double2) * nhi, "float-float twiddles"));
+        FCAS_TRY(dev_alloc(&c->d_stw_aff, sizeof(double2) << kMaxLogPass, "float-float stage twiddles"));
+        FCAS_TRY(dev_alloc(&c->d_stw_bff, sizeof(double2) << kMaxLogPass, "float-float stage twiddles"));
+        FCAS_TRYCUDA(launch_split_ff(c->d_twlo64, c->d_twloff, (int64_t)nlo, st));
+        FCAS_TRYCUDA(launch_split_ff(c->d_twhi64, c->d_twhiff, (int64_t)nhi, st));
+    }
 
     // forward FFT of the data (binary64) and the whitened, re-laid-out band spectrum
     FCAS_TRY(dev_alloc(&d_spec, sizeof(double2) * (size_t)D * n, "data spectrum"));
@@ -506,7 +516,7 @@ int fcas_fitness(fcas_ctx* c, int64_t n, const double* theta, double* fitness, i
     if (!f_dev) FCAS_CUDA(cudaMemcpyAsync(fitness, d_fit, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, st));
     if (!t_dev) FCAS_CUDA(cudaMemcpyAsync(tc, d_tc, sizeof(int64_t) * (size_t)n, cudaMemcpyDeviceToHost, st));
     if (!th_dev || !f_dev || !t_dev) FCAS_CUDA(cudaStreamSynchronize(st));
-    if (const unsigned int bad = take_index_checks(st))
+    if (const unsigned int bad = take_index_checks(st) | take_index_checks_ff(st))
         return fail(FCAS_ERR_CUDA, "fcas_fitness: index checks failed (bits 0x%x)", bad);
     return FCAS_OK;
 }

@@ -78,6 +78,22 @@ cudaError_t launch_time_shift(const double* x, double* y, int n_det, int64_t n, 
     return cudaGetLastError();
 }
 
+__global__ void split_ff_kernel(const double2* __restrict__ src, float4* __restrict__ dst, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 v = src[i];
+        const float xh = (float)v.x, yh = (float)v.y;
+        dst[i] = make_float4(xh, (float)(v.x - (double)xh), yh, (float)(v.y - (double)yh));
+    }
+}
+
+cudaError_t launch_split_ff(const double2* src, void* dst, int64_t n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    split_ff_kernel<<<(unsigned)blocks, 256, 0, s>>>(src, static_cast<float4*>(dst), n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_check_finite(const double* x, int64_t n, int* flag, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     int64_t blocks = (n + 255) / 256;

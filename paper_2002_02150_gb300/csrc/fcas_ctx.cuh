@@ -3,6 +3,7 @@
 
 #include <vector>
 
+#include "fcas_ff.cuh"
 #include "fcas_kernels.cuh"
 
 namespace fcas {
@@ -53,6 +54,10 @@ struct fcas_ctx {
     float2* d_stw_a32 = nullptr;
     double2* d_stw_b64 = nullptr;   // per-stage twiddles, length-N1 transforms
     float2* d_stw_b32 = nullptr;
+    void* d_twloff = nullptr;       // float-float copies (16-byte entries) of twlo, twhi and the
+    void* d_twhiff = nullptr;       // stage tables (FCAS_PREC_FF contexts only)
+    void* d_stw_aff = nullptr;
+    void* d_stw_bff = nullptr;
     fcas::ParticleParams* d_params = nullptr;
     int64_t params_cap = 0;
     double* d_theta = nullptr;      // staging for host theta
@@ -80,6 +85,20 @@ struct fcas_ctx {
 namespace fcas {
 
 // Pointers and sizes the fitness kernels need, taken from a prepared context.
+// Pass A / pass B of one chunk in the context's form.
+inline cudaError_t launch_pass_a_prec(int precision, const FitnessPlan& plan, const ParticleParams* params, int64_t p0,
+                                      int64_t np, void* inter, cudaStream_t st) {
+    if (precision == FCAS_PREC_FP32) return launch_pass_a<float>(plan, params, p0, np, inter, st);
+    if (precision == FCAS_PREC_FF) return launch_pass_a<ffloat>(plan, params, p0, np, inter, st);
+    return launch_pass_a<double>(plan, params, p0, np, inter, st);
+}
+inline cudaError_t launch_pass_b_prec(int precision, const FitnessPlan& plan, const ParticleParams* params, int64_t p0,
+                                      int64_t np, const void* inter, Partial* partials, cudaStream_t st) {
+    if (precision == FCAS_PREC_FP32) return launch_pass_b<float>(plan, params, p0, np, inter, partials, st);
+    if (precision == FCAS_PREC_FF) return launch_pass_b<ffloat>(plan, params, p0, np, inter, partials, st);
+    return launch_pass_b<double>(plan, params, p0, np, inter, partials, st);
+}
+
 inline FitnessPlan make_plan(const fcas_ctx* c) {
     FitnessPlan p;
     p.n_det = c->setup.n_det;
@@ -87,16 +106,16 @@ inline FitnessPlan make_plan(const fcas_ctx* c) {
     p.log_n1 = c->log_n1;
     p.log_n2 = c->log_n2;
     p.n_samples = c->setup.n_samples;
-    const bool fp32 = c->setup.precision == FCAS_PREC_FP32;
+    const bool fp32 = c->setup.precision == FCAS_PREC_FP32, ff = c->setup.precision == FCAS_PREC_FF;
     p.y = c->d_y;
     p.basis = c->d_basis;
-    p.stw_a = fp32 ? (const void*)c->d_stw_a32 : (const void*)c->d_stw_a64;
-    p.stw_b = fp32 ? (const void*)c->d_stw_b32 : (const void*)c->d_stw_b64;
+    p.stw_a = fp32 ? (const void*)c->d_stw_a32 : ff ? (const void*)c->d_stw_aff : (const void*)c->d_stw_a64;
+    p.stw_b = fp32 ? (const void*)c->d_stw_b32 : ff ? (const void*)c->d_stw_bff : (const void*)c->d_stw_b64;
     p.k1b = c->k1b;
     p.radix_bits_a = c->radix_bits_a;
     p.sub = c->sub;
-    p.tw_lo = c->d_twlo;
-    p.tw_hi = c->d_twhi;
+    p.tw_lo = ff ? c->d_twloff : c->d_twlo;
+    p.tw_hi = ff ? c->d_twhiff : c->d_twhi;
     return p;
 }
 

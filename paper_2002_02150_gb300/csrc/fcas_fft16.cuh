@@ -19,8 +19,20 @@
 #pragma once
 
 #include "fcas_internal.cuh"
+#include "fcas_ff.cuh"
 
 namespace fcas {
+
+template <> struct cplx_of<ffloat> { using type = ff2; };
+
+// read-only cached load of a complex table entry
+__device__ __forceinline__ float2 ldg_c(const float2* p) { return __ldg(p); }
+__device__ __forceinline__ double2 ldg_c(const double2* p) { return __ldg(p); }
+__device__ __forceinline__ ff2 ldg_c(const ff2* p) {
+    const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+    return ff2{ffloat(q.x, q.y), ffloat(q.z, q.w)};
+}
+template <int SGN, typename R> __device__ __forceinline__ R sgn_mul(R v) { return SGN > 0 ? v : -v; }
 
 // MAXRB: radix bits of the full stages (4: radix 16, 16 values per thread; 3: radix 8, 8 values)
 __host__ __device__ constexpr int fftr_radix_bits(int log_l, int done, int maxrb) {
@@ -80,14 +92,14 @@ __device__ __forceinline__ C rot16(C x) {
                                    1.0, 0.92387953251128675613, 0.70710678118654752440, 0.38268343236508977173,
                                    0.0, -0.38268343236508977173, -0.70710678118654752440, -0.92387953251128675613,
                                    -1.0, -0.92387953251128675613, -0.70710678118654752440, -0.38268343236508977173};
-        const R c = (R)kC[m];
-        const R s = (R)(S * kS[m]);
         if constexpr (m == 2 || m == 6 || m == 10 || m == 14) {
             // |c| = |s| = 1/sqrt 2: two multiplies instead of four
             const R k = (R)0.70710678118654752440;
-            const R sc = c > 0 ? (R)1 : (R)-1, ss = s > 0 ? (R)1 : (R)-1;
-            return mkc(k * (sc * x.x - ss * x.y), k * (ss * x.x + sc * x.y));
+            constexpr int sc = kC[m] > 0 ? 1 : -1, ss = S * kS[m] > 0 ? 1 : -1;
+            return mkc(k * (sgn_mul<sc>(x.x) - sgn_mul<ss>(x.y)), k * (sgn_mul<ss>(x.x) + sgn_mul<sc>(x.y)));
         } else {
+            const R c = (R)kC[m];
+            const R s = (R)(S * kS[m]);
             return mkc(x.x * c - x.y * s, x.x * s + x.y * c);
         }
     }
@@ -202,8 +214,8 @@ __device__ __forceinline__ void fftr_stage(cplx<Real> (&v)[fftr_v(LOG_L, MAXRB)]
                 // w^r for r = 1..R-1 from two table entries: w and w^4 (powers by products, <= 3 roundings)
                 C w1 = mkc((Real)1, (Real)0), w4 = w1;
                 if (FCAS_CHECK((NS - 1) + jm + 3 * NS < L, kCheckTwiddle)) {
-                    w1 = __ldg(t);
-                    w4 = __ldg(t + 3 * NS);
+                    w1 = ldg_c(t);
+                    w4 = ldg_c(t + 3 * NS);
                 }
                 if constexpr (S < 0) {
                     w1 = cconj(w1);
@@ -227,7 +239,7 @@ __device__ __forceinline__ void fftr_stage(cplx<Real> (&v)[fftr_v(LOG_L, MAXRB)]
 #pragma unroll
                 for (int r = 1; r < R; ++r) {
                     C w = mkc((Real)1, (Real)0);
-                    if (FCAS_CHECK((NS - 1) + (r - 1) * NS + jm < L, kCheckTwiddle)) w = __ldg(t + (r - 1) * NS);
+                    if (FCAS_CHECK((NS - 1) + (r - 1) * NS + jm < L, kCheckTwiddle)) w = ldg_c(t + (r - 1) * NS);
                     if constexpr (S < 0) w = cconj(w);
                     a[r] = cmul(a[r], w);
                 }

@@ -1,17 +1,7 @@
-// Fitness path: per-particle geometry, pass A (fused template x data x delay phase feeding the
-// first FFT pass), pass B (second FFT pass + antenna projection + partial argmax over t_c) and
-// the final argmax. The length-N inverse transform over t_c is split as N = N1 N2 with
-// k = k1 + N1 k2 and t = ta + N2 tb:
-//   Z[ta + N2 tb] = sum_k1 e^{2 pi i k1 tb / N1} [ e^{2 pi i k1 ta / N} sum_k2 Q[k1 + N1 k2] e^{2 pi i k2 ta / N2} ]
-// Pass A computes the bracket for every column k1 (length-N2 transforms) and stores it as
-// A[ta][k1]; pass B transforms every row ta over k1 (length N1). Only two series per particle
-// cross between the passes: the detector sum is taken with the network weights before the
-// transform (see pass A).
-#include <cfloat>
-#include <climits>
-
-#include "fcas_fft16.cuh"
-#include "fcas_kernels.cuh"
+// Fitness path, per-particle and host-side parts: geometry, the final argmax, the shape helpers
+// of the two passes, the per-stage twiddle tables, and the FP32 / binary64 instantiations of the
+// passes (fcas_passes.cuh).
+#include "fcas_passes.cuh"
 
 namespace fcas {
 
@@ -128,317 +118,6 @@ cudaError_t launch_geometry(const double* theta, int64_t n, ParticleParams* out,
     return cudaGetLastError();
 }
 
-// ------------------------------------------------------------------------------------------
-// Phase of Q_i[k] = Y_i[k] e^{2 pi i (psi(f_k)/2pi + f_k Delta^i)} (Sec. II.B, eq. data_template_innprod)
-// ------------------------------------------------------------------------------------------
-
-// frac((ah + al)(bh + bl)) with the leading product split exactly: the result is the product
-// reduced by an integer, accurate to a few float ulps of 1 turn.
-__device__ __forceinline__ float frac_mul_ff(float ah, float al, float bh, float bl) {
-    const float p = __fmul_rn(ah, bh);
-    float e = __fmaf_rn(ah, bh, -p);
-    e = __fmaf_rn(ah, bl, e);
-    e = __fmaf_rn(al, bh, e);
-    return __fadd_rn(__fsub_rn(p, rintf(p)), e);
-}
-
-__device__ __forceinline__ float round_nearest(float x) { return rintf(x); }
-__device__ __forceinline__ double round_nearest(double x) { return rint(x); }
-
-__device__ __forceinline__ double chirp_frac(const BasisD& b, const ParticleParams& pp) {
-    double s = pp.c[0] * b.a.x + pp.c[1] * b.a.y + pp.c[2] * b.b.x + pp.c[3] * b.b.y;
-    return s - rint(s);
-}
-
-// e^{2 pi i turns} for |turns| <= 1/2 with the hardware sine/cosine (absolute error ~4e-7 on
-// [-pi, pi], far below the FP32 form's tolerance)
-__device__ __forceinline__ float2 fast_phasor(float turns) {
-    float sn, cs;
-    __sincosf(6.2831853071795865f * turns, &sn, &cs);
-    return make_float2(cs, sn);
-}
-
-__device__ __forceinline__ float2 unit_phasor(float turns) {
-    float sn, cs;
-    sincospif(2.0f * turns, &sn, &cs);
-    return make_float2(cs, sn);
-}
-__device__ __forceinline__ double2 unit_phasor(double turns) {
-    double sn, cs;
-    sincospi(2.0 * turns, &sn, &cs);
-    return make_double2(cs, sn);
-}
-
-// ------------------------------------------------------------------------------------------
-// Pass A: for every band bin of the CTA's columns, Q_i[k] = Y_i[k] e^{2 pi i (psi(f_k)/2pi + f_k Delta^i)}
-// is generated on the load and combined over detectors into the two network-weighted spectra
-// P_a[k] = sum_i w_a,i Q_i[k] (a = 1, 2); each is transformed over k2 (length N2) and twiddled by
-// e^{2 pi i k1 ta / N}. By linearity of the transform over t_c, Z-projections
-// W_a(t) = sum_i w_a,i Z_i(t) are the transforms of P_a (Sec. II.C projection applied before the
-// t_c scan instead of after it).
-// ------------------------------------------------------------------------------------------
-// Pass A keeps two FFT exchange buffers when both fit in 200 KB of shared memory.
-template <typename Real, int LOG_L, int K1B>
-__host__ __device__ constexpr bool pass_a_pingpong() {
-    return 2 * sizeof(cplx<Real>) * (size_t)K1B * fft16_buf_elems(LOG_L) <= 200 * 1024;
-}
-
-template <typename Real>
-struct DetConst {
-    Real dh[FCAS_MAX_DET], dl[FCAS_MAX_DET], w1[FCAS_MAX_DET], w2[FCAS_MAX_DET];
-};
-
-template <typename Real, int LOG_L, int K1B, int MAXRB>
-__global__ void __launch_bounds__(K1B * ((1 << LOG_L) / fftr_v(LOG_L, MAXRB)), 1)
-pass_a_kernel(const cplx<Real>* __restrict__ y, const Basis<Real>* __restrict__ basis,
-              const ParticleParams* __restrict__ params, int64_t p0, int64_t np, int n_det, int log_n1, int sub_req,
-              cplx<Real>* __restrict__ out, const cplx<Real>* __restrict__ stw,
-              const cplx<Real>* __restrict__ tw_lo, const cplx<Real>* __restrict__ tw_hi) {
-    using C = cplx<Real>;
-    constexpr int L = 1 << LOG_L;
-    constexpr int V = fftr_v(LOG_L, MAXRB);
-    constexpr int G = L / V;
-    constexpr int VH = V / 2;    // values with k2 < L/2; the rest of the column is zero (k >= N/2)
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* smem = reinterpret_cast<C*>(smem_raw);
-    __shared__ DetConst<Real> sc;
-
-    const int c = threadIdx.x % K1B;
-    const int j = threadIdx.x / K1B;
-    // CTA order: SUB adjacent column blocks of one particle, then the particles of the chunk, then
-    // the next group of column blocks. The SUB CTAs fill whole 128-byte lines of each output row
-    // together (so L2 merges them before write-back) and the chunk's particles read the same
-    // spectrum block close in time (so it is fetched from DRAM once).
-    const int nblk = (1 << log_n1) / K1B;
-    const int sub = sub_req < nblk ? sub_req : nblk;
-    const int64_t lin = blockIdx.x;
-    const int64_t rest = lin / sub;
-    const int64_t p = rest % np;
-    const int blk = (int)((rest / np) * sub + lin % sub);
-    const int k1 = blk * K1B + c;
-    const ParticleParams* pp = params + p0 + p;
-    if (!pp->valid) return;   // not evaluated (invalid input, or a PSO particle outside its box)
-    if (threadIdx.x < FCAS_MAX_DET) {
-        const int i = threadIdx.x;
-        if constexpr (sizeof(Real) == 4) {
-            sc.dh[i] = pp->dh[i];
-            sc.dl[i] = pp->dl[i];
-            sc.w1[i] = pp->w1f[i];
-            sc.w2[i] = pp->w2f[i];
-        } else {
-            sc.dh[i] = pp->dturn[i];
-            sc.dl[i] = 0.0;
-            sc.w1[i] = pp->w1[i];
-            sc.w2[i] = pp->w2[i];
-        }
-    }
-    __syncthreads();
-    const int n1 = 1 << log_n1;
-
-    // Thread (c, j) owns the bins k = k1 + N1 (j + q G), q < VH. The delay phasors e^{2 pi i k Delta^i / T}
-    // of consecutive q differ by the constant factor e^{2 pi i N1 G Delta^i / T}: one accurate phasor
-    // and one step per detector, then products. The chirp phasor multiplies the detector sums last:
-    // P_a[k] = e^{i psi(f_k)} sum_i w_a,i Y_i[k] e^{2 pi i f_k Delta^i}.
-    C r1[VH], r2[VH];
-#pragma unroll
-    for (int q = 0; q < VH; ++q) r1[q] = r2[q] = mkc((Real)0, (Real)0);
-    // the chirp basis of the thread's bins is requested first: its latency overlaps the detector sums
-    const Basis<Real>* bb = basis + ((int64_t)blk * (L / 2) + j) * K1B + c;
-    Basis<Real> bq[sizeof(Real) == 4 ? VH : 1];
-    if constexpr (sizeof(Real) == 4) {
-#pragma unroll
-        for (int q = 0; q < VH; ++q)
-            if (FCAS_CHECK(((int64_t)blk * (L / 2) + j) * K1B + c + (int64_t)q * G * K1B < ((int64_t)L / 2 << log_n1),
-                           kCheckBasis))
-                bq[q] = bb[(int64_t)q * G * K1B];
-    }
-    const int kbase = k1 + n1 * j;
-    const int kstep = n1 * G;
-    const int64_t col0 = (int64_t)blk * n_det;
-#pragma unroll
-    for (int i = 0; i < FCAS_MAX_DET; ++i) {
-        if (i >= n_det) break;
-        C dph, dstep;
-        if constexpr (sizeof(Real) == 4) {
-            float fb = frac_mul_ff((float)kbase, 0.0f, sc.dh[i], sc.dl[i]);
-            float fs = frac_mul_ff((float)kstep, 0.0f, sc.dh[i], sc.dl[i]);
-            fb -= rintf(fb);
-            fs -= rintf(fs);
-            dph = fast_phasor(fb);
-            dstep = fast_phasor(fs);
-        } else {
-            double fb = (double)kbase * sc.dh[i], fs = (double)kstep * sc.dh[i];
-            dph = unit_phasor(fb - rint(fb));
-            dstep = unit_phasor(fs - rint(fs));
-        }
-        const C* yd = y + ((col0 + i) * (L / 2) + j) * K1B + c;
-        const Real w1 = sc.w1[i], w2 = sc.w2[i];
-#pragma unroll
-        for (int q = 0; q < VH; ++q) {
-            C yv = mkc((Real)0, (Real)0);
-            if (FCAS_CHECK(((col0 + i) * (L / 2) + j) * K1B + c + (int64_t)q * G * K1B <
-                               (int64_t)n_det * ((int64_t)L / 2 << log_n1), kCheckSpectrum))
-                yv = yd[(int64_t)q * G * K1B];
-            const C t = cmul(yv, dph);
-            r1[q].x += w1 * t.x;
-            r1[q].y += w1 * t.y;
-            r2[q].x += w2 * t.x;
-            r2[q].y += w2 * t.y;
-            if (q + 1 < VH) dph = cmul(dph, dstep);
-        }
-    }
-    {
-        float cfh[4], cfl[4];
-        if constexpr (sizeof(Real) == 4) {
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                cfh[r] = pp->ch[r];
-                cfl[r] = pp->cl[r];
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < VH; ++q) {
-            C cp;
-            if constexpr (sizeof(Real) == 4) {
-                const ChirpPowers b = chirp_powers(bq[q]);
-                float s = frac_mul_ff(cfh[0], cfl[0], b.b53.x, b.b53.y);
-                s += frac_mul_ff(cfh[1], cfl[1], b.b1.x, b.b1.y);
-                s += frac_mul_ff(cfh[2], cfl[2], b.b23.x, b.b23.y);
-                s += frac_mul_ff(cfh[3], cfl[3], b.b13.x, b.b13.y);
-                cp = fast_phasor(s - rintf(s));
-            } else {
-                Basis<Real> b{};
-                if (FCAS_CHECK(((int64_t)blk * (L / 2) + j) * K1B + c + (int64_t)q * G * K1B <
-                                   ((int64_t)L / 2 << log_n1), kCheckBasis))
-                    b = bb[(int64_t)q * G * K1B];
-                cp = unit_phasor(chirp_frac(b, *pp));
-            }
-            r1[q] = cmul(r1[q], cp);
-            r2[q] = cmul(r2[q], cp);
-        }
-    }
-
-#pragma unroll 1
-    for (int a = 0; a < kSeries; ++a) {
-        C v[V];
-#pragma unroll
-        for (int q = 0; q < VH; ++q) v[q] = a == 0 ? r1[q] : r2[q];
-#pragma unroll
-        for (int q = VH; q < V; ++q) v[q] = mkc((Real)0, (Real)0);
-        // two exchange buffers where shared memory allows (no barrier before each exchange write); the
-        // exchange count is continued across the series so that a buffer is never rewritten before
-        // all its reads of the previous exchange are done
-        constexpr int NX = (LOG_L + MAXRB - 1) / MAXRB - 1;
-        fftr<Real, +1, LOG_L, MAXRB, pass_a_pingpong<Real, LOG_L, K1B>()>(v, smem + c, K1B, j, stw,
-                                                                          K1B * fft16_buf_elems(LOG_L), (a * NX) & 1);
-        C* orow = out + ((p * kSeries + a) * L) * (int64_t)n1 + k1;
-        // e^{2 pi i k1 ta / N} for ta = j + q G: the value at q = 0 times powers of the step e^{2 pi i k1 G / N}
-        const int m0 = k1 * j, ms = k1 * G;   // < N
-        C w = cmul(__ldg(tw_hi + (m0 >> kTwLoBits)), __ldg(tw_lo + (m0 & ((1 << kTwLoBits) - 1))));
-        const C step = cmul(__ldg(tw_hi + (ms >> kTwLoBits)), __ldg(tw_lo + (ms & ((1 << kTwLoBits) - 1))));
-#pragma unroll
-        for (int q = 0; q < V; ++q) {
-            const int ta = j + q * G;
-            if (FCAS_CHECK((p * kSeries + a) * (int64_t)L * n1 + k1 + (int64_t)ta * n1 < np * kSeries * (int64_t)L * n1,
-                           kCheckInterWrite))
-                __stcs(orow + (int64_t)ta * n1, cmul(v[q], w));   // streamed: read back only by pass B
-            if (q + 1 < V) w = cmul(w, step);
-        }
-    }
-}
-
-// ------------------------------------------------------------------------------------------
-// Pass B: transforms every row ta of both series over k1 (length N1), Gamma^2(t) = |W1(t)|^2 +
-// |W2(t)|^2 for t = ta + N2 tb (Sec. II.C, the maximisation over A_k in closed form), and the
-// argmax over the CTA's rows (lowest t on ties).
-// ------------------------------------------------------------------------------------------
-// Resident pass-B CTAs per SM the compiler is held to: three for the FP32 form's 2^11- and
-// 2^12-point rows (76-77 registers, no spills), two for other CTAs of up to 256 threads.
-__host__ __device__ constexpr int pass_b_min_blocks(int log_l, int real_bytes) {
-    return pass_b_threads(log_l, real_bytes) > 256 ? 1 : (real_bytes == 4 && (log_l == 11 || log_l == 12)) ? 3 : 2;
-}
-
-template <typename Real, int LOG_L>
-__global__ void __launch_bounds__(pass_b_threads(LOG_L, sizeof(Real)), pass_b_min_blocks(LOG_L, sizeof(Real)))
-pass_b_kernel(const cplx<Real>* __restrict__ inter, const ParticleParams* __restrict__ params, int64_t p0,
-              int log_n2, int64_t n_samples, const cplx<Real>* __restrict__ stw, Partial* __restrict__ partials) {
-    using C = cplx<Real>;
-    constexpr int L = 1 << LOG_L;
-    constexpr int V = shape_v(LOG_L);
-    constexpr int G = L / V;
-    constexpr int TB = pass_b_tb(LOG_L, sizeof(Real));
-    constexpr int NT = TB * G;
-    constexpr int BUF = fft16_buf_elems(LOG_L);
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* smem = reinterpret_cast<C*>(smem_raw);
-    constexpr int NRED = NT >= 32 ? NT / 32 : NT;
-    __shared__ Real red_v[NRED];
-    __shared__ int red_t[NRED];
-
-    const int j = threadIdx.x % G;
-    const int c = threadIdx.x / G;
-    const int n2 = 1 << log_n2;
-    const int ta = blockIdx.x * TB + c;
-    const int64_t p = blockIdx.y;
-    if (!params[p0 + p].valid) return;   // the final reduce reports NaN for it
-
-    Real g[V];
-#pragma unroll
-    for (int q = 0; q < V; ++q) g[q] = (Real)0;
-#pragma unroll 1
-    for (int a = 0; a < kSeries; ++a) {
-        const C* row = inter + ((p * kSeries + a) * n2 + ta) * (int64_t)L;
-        C v[V];
-#pragma unroll
-        for (int q = 0; q < V; ++q)
-            if (FCAS_CHECK(((p * kSeries + a) * n2 + ta) * (int64_t)L + j + q * G < (int64_t)gridDim.y * kSeries * n2 * L,
-                           kCheckInterRead))
-                v[q] = row[j + q * G];
-        fft16<Real, +1, LOG_L>(v, smem + c * BUF, 1, j, stw);
-#pragma unroll
-        for (int q = 0; q < V; ++q) g[q] += v[q].x * v[q].x + v[q].y * v[q].y;
-    }
-    // t = ta + N2 (j + q G) grows with q, so a strict comparison keeps the lowest t among equal values
-    Real best = (Real)-1;
-    int bt = INT_MAX;
-#pragma unroll
-    for (int q = 0; q < V; ++q) {
-        const int t = ta + n2 * (j + q * G);
-        if (t < n_samples && g[q] > best) {
-            best = g[q];
-            bt = t;
-        }
-    }
-    if constexpr (NT >= 32) {
-        // NT is a multiple of 32: every warp is full
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            const Real ov = __shfl_down_sync(0xffffffffu, best, off);
-            const int ot = __shfl_down_sync(0xffffffffu, bt, off);
-            if (ov > best || (ov == best && ot < bt)) { best = ov; bt = ot; }
-        }
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        if (lane == 0) { red_v[warp] = best; red_t[warp] = bt; }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            for (int w = 1; w < NT / 32; ++w)
-                if (red_v[w] > best || (red_v[w] == best && red_t[w] < bt)) { best = red_v[w]; bt = red_t[w]; }
-        }
-    } else {
-        // fewer than 32 threads: no shuffles over lanes that do not exist
-        red_v[threadIdx.x] = best;
-        red_t[threadIdx.x] = bt;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            for (int w = 1; w < NT; ++w)
-                if (red_v[w] > best || (red_v[w] == best && red_t[w] < bt)) { best = red_v[w]; bt = red_t[w]; }
-        }
-    }
-    if (threadIdx.x == 0)
-        partials[p * gridDim.x + blockIdx.x] = Partial{bt == INT_MAX ? -DBL_MAX : (double)best,
-                                                       bt == INT_MAX ? INT64_MAX : (int64_t)bt};
-}
-
 __device__ __forceinline__ bool better(double v, int64_t t, double bv, int64_t bt) {
     return v > bv || (v == bv && t < bt);
 }
@@ -481,10 +160,8 @@ cudaError_t launch_reduce(const Partial* partials, int64_t nb, const ParticlePar
 }
 
 // ------------------------------------------------------------------------------------------
-// dispatch on the transform lengths
+// shape helpers of the passes
 // ------------------------------------------------------------------------------------------
-#define FCAS_LOG_CASES(X) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13)
-
 int pass_a_k1b_for(int log_n2, int precision) {
     const int rb = precision == FCAS_PREC_FP32 ? 4 : 8;
     switch (log_n2) {
@@ -503,51 +180,6 @@ int pass_b_blocks_per_particle(int log_n1, int log_n2, int precision) {
 #undef FCAS_CASE
         default: return -1;
     }
-}
-
-template <typename Real, int LG, int K1B, int MAXRB = 4>
-static cudaError_t pass_a_at(const FitnessPlan& pl, const ParticleParams* params, int64_t p0, int64_t np, void* inter,
-                             cudaStream_t s) {
-    constexpr int THREADS = K1B * ((1 << LG) / fftr_v(LG, MAXRB));
-    const size_t smem = (pass_a_pingpong<Real, LG, K1B>() ? 2 : 1) * sizeof(cplx<Real>) * (size_t)K1B * fft16_buf_elems(LG);
-    auto kern = pass_a_kernel<Real, LG, K1B, MAXRB>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    const int64_t ctas = np * ((1 << pl.log_n1) / K1B);
-    kern<<<(unsigned)ctas, THREADS, smem, s>>>(static_cast<const cplx<Real>*>(pl.y),
-                                     static_cast<const Basis<Real>*>(pl.basis),
-                                     params, p0, np, pl.n_det, pl.log_n1, pl.sub, static_cast<cplx<Real>*>(inter),
-                                     static_cast<const cplx<Real>*>(pl.stw_a), static_cast<const cplx<Real>*>(pl.tw_lo),
-                                     static_cast<const cplx<Real>*>(pl.tw_hi));
-    return cudaGetLastError();
-}
-
-// Column-block widths compiled for pass A: the default of the length and, for the FP32 form at
-// lengths >= 2^8, half and twice it (the autotuner's choices).
-template <int LG, int RB>
-constexpr bool k1b_variant_ok(int k) {
-    return k >= 1 && k <= 16 && k <= (1 << LG) && k * ((1 << LG) / shape_v(LG)) <= 1024;
-}
-
-template <typename Real, int LG>
-static cudaError_t pass_a_lg(const FitnessPlan& pl, const ParticleParams* params, int64_t p0, int64_t np,
-                             void* inter, cudaStream_t s) {
-    constexpr int RB = sizeof(Real);
-    constexpr int KD = pass_a_k1b(LG, RB);
-    if (pl.radix_bits_a == 3) {
-        // radix-8 stages: 8 values per thread, 1024-thread CTAs of 4 columns (FP32, >= 2^10 points)
-        if constexpr (RB == 4 && LG >= 10 && LG <= 12)
-            if (pl.k1b == 4) return pass_a_at<Real, LG, 4, 3>(pl, params, p0, np, inter, s);
-        return cudaErrorInvalidValue;
-    }
-    if (pl.k1b == KD) return pass_a_at<Real, LG, KD>(pl, params, p0, np, inter, s);
-    if constexpr (RB == 4 && LG >= 8) {
-        if constexpr (k1b_variant_ok<LG, RB>(KD / 2))
-            if (pl.k1b == KD / 2) return pass_a_at<Real, LG, (KD / 2 > 0 ? KD / 2 : 1)>(pl, params, p0, np, inter, s);
-        if constexpr (k1b_variant_ok<LG, RB>(KD * 2))
-            if (pl.k1b == KD * 2) return pass_a_at<Real, LG, (KD * 2 <= 16 ? KD * 2 : 16)>(pl, params, p0, np, inter, s);
-    }
-    return cudaErrorInvalidValue;
 }
 
 bool pass_a_radix8_available(int log_n2, int precision, int k1b) {
@@ -571,45 +203,6 @@ int pass_a_k1b_variants(int log_n2, int precision, int* out) {
         FCAS_LOG_CASES(FCAS_CASE)
 #undef FCAS_CASE
         default: return 0;
-    }
-}
-
-template <typename Real, int LG>
-static cudaError_t pass_b_at(const FitnessPlan& pl, const ParticleParams* params, int64_t p0, int64_t np,
-                             const void* inter, Partial* partials, cudaStream_t s) {
-    constexpr int TB = pass_b_tb(LG, sizeof(Real));
-    constexpr int THREADS = pass_b_threads(LG, sizeof(Real));
-    const size_t smem = sizeof(cplx<Real>) * (size_t)TB * fft16_buf_elems(LG);
-    auto kern = pass_b_kernel<Real, LG>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)((1 << pl.log_n2) / TB), (unsigned)np);
-    kern<<<grid, THREADS, smem, s>>>(static_cast<const cplx<Real>*>(inter), params, p0, pl.log_n2, pl.n_samples,
-                                     static_cast<const cplx<Real>*>(pl.stw_b), partials);
-    return cudaGetLastError();
-}
-
-template <typename Real>
-cudaError_t launch_pass_a(const FitnessPlan& pl, const ParticleParams* params, int64_t p0, int64_t np, void* inter,
-                          cudaStream_t s) {
-    if (np <= 0) return cudaSuccess;
-    switch (pl.log_n2) {
-#define FCAS_CASE(LG) case LG: return pass_a_lg<Real, LG>(pl, params, p0, np, inter, s);
-        FCAS_LOG_CASES(FCAS_CASE)
-#undef FCAS_CASE
-        default: return cudaErrorInvalidValue;
-    }
-}
-
-template <typename Real>
-cudaError_t launch_pass_b(const FitnessPlan& pl, const ParticleParams* params, int64_t p0, int64_t np,
-                          const void* inter, Partial* partials, cudaStream_t s) {
-    if (np <= 0) return cudaSuccess;
-    switch (pl.log_n1) {
-#define FCAS_CASE(LG) case LG: return pass_b_at<Real, LG>(pl, params, p0, np, inter, partials, s);
-        FCAS_LOG_CASES(FCAS_CASE)
-#undef FCAS_CASE
-        default: return cudaErrorInvalidValue;
     }
 }
 

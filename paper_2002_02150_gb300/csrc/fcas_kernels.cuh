@@ -95,6 +95,9 @@ int pass_b_blocks_per_particle(int log_n1, int log_n2, int precision);
 // Checked build (FCAS_CHECKED): waits for the stream, returns and clears the bits of the index
 // checks that failed since the last call (see fcas_fft16.cuh). Other builds: 0, no synchronisation.
 unsigned int take_index_checks(cudaStream_t s);
+// float-float copy (16-byte entries: hi/lo of re, hi/lo of im) of a binary64 complex table
+cudaError_t launch_split_ff(const double2* src, void* dst, int64_t n, cudaStream_t s);
+unsigned int take_index_checks_ff(cudaStream_t s);   // the float-float passes' translation unit
 int pass_a_k1b_for(int log_n2, int precision);
 // compiled pass-A column-block widths for a length: writes up to 3 values, returns the count
 int pass_a_k1b_variants(int log_n2, int precision, int* out);

@@ -82,7 +82,7 @@ extern "C" int fcas_fitness_noalloc(const fcas_ctx* c, int64_t n, const double* 
         snprintf(msg, sizeof(msg),
                  "fcas_fitness_noalloc: one particle needs %zu bytes of scratch (n_det = %d, n_fft = %lld, %s) but the "
                  "static scratch holds %zu bytes; use fcas_fitness for this segment",
-                 per_particle, c->setup.n_det, (long long)c->setup.n_fft, fp32 ? "FP32" : "FP64", kStaticScratchBytes);
+                 per_particle, c->setup.n_det, (long long)c->setup.n_fft, fp32 ? "FP32" : "FP64/FF", kStaticScratchBytes);
         return report_error(FCAS_ERR_INVALID, msg);
     }
     // scratch layout for `cap` particles: parameters | argmax partials | intermediate transform.
@@ -100,11 +100,8 @@ extern "C" int fcas_fitness_noalloc(const fcas_ctx* c, int64_t n, const double* 
         e = launch_geometry(theta + 4 * p0, np, params, c->d_det, c->d_sigma2s, c->setup.n_det, c->setup.f_low, c->df,
                             st);
         if (e == cudaSuccess)
-            e = fp32 ? launch_pass_a<float>(plan, params, 0, np, inter, st)
-                     : launch_pass_a<double>(plan, params, 0, np, inter, st);
-        if (e == cudaSuccess)
-            e = fp32 ? launch_pass_b<float>(plan, params, 0, np, inter, partials, st)
-                     : launch_pass_b<double>(plan, params, 0, np, inter, partials, st);
+            e = launch_pass_a_prec(c->setup.precision, plan, params, 0, np, inter, st);
+        if (e == cudaSuccess) e = launch_pass_b_prec(c->setup.precision, plan, params, 0, np, inter, partials, st);
         if (e == cudaSuccess) e = launch_reduce(partials, c->nb_partials, params, 0, np, fitness + p0, tc + p0, st);
     }
     if (e != cudaSuccess) return report_error(FCAS_ERR_CUDA, cudaGetErrorString(e));

@@ -18,6 +18,7 @@ LIB_PATH = os.environ.get("FCAS_LIBRARY") or os.path.join(_HERE, "libfcas.so")
 FCAS_MAX_DET = 8
 FCAS_PREC_FP64 = 0
 FCAS_PREC_FP32 = 1
+FCAS_PREC_FF = 2      # float-float transforms: binary64-class accuracy on the FP32 units
 KERNEL_KINDS = {"geometry": 0, "pass_a": 1, "pass_b": 2, "reduce": 3}
 
 
@@ -207,7 +208,8 @@ def fcas_create(det, psd, data, n_fft, fs, f_low, f_high, precision="fp32", max_
         dets[i].xarm[:] = det[i, 3:6]
         dets[i].yarm[:] = det[i, 6:9]
     n_samples = int(data.shape[-1])
-    prec = {"fp32": FCAS_PREC_FP32, "fp64": FCAS_PREC_FP64}[precision] if isinstance(precision, str) else int(precision)
+    prec = ({"fp32": FCAS_PREC_FP32, "fp64": FCAS_PREC_FP64, "ff": FCAS_PREC_FF}[precision] if isinstance(precision, str)
+            else int(precision))
     setup = fcas_setup(n_det, prec, n_samples, int(n_fft), float(fs), float(f_low), float(f_high), int(max_batch),
                        int(flags))
     p_psd, k1 = _ptr(psd, np.float64)

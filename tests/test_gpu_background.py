@@ -27,7 +27,7 @@ def _rolled(data, shifts):
     return out
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("precision", ["fp32", "fp64", "ff"])
 def test_time_shifted_context_equals_a_context_of_the_rolled_data(precision):
     import paper_2002_02150_gb300 as fc
     w = sd.SMALL

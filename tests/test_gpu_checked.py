@@ -68,10 +68,11 @@ def _cases(fc):
     for n_fft, n_samples, fs, f_low, f_high in SIZES:
         kw = dict(base="SMALL", n_fft=n_fft, n_samples=n_samples, fs=fs, f_low=f_low, f_high=f_high,
                   arrival_s=0.3 * n_samples / fs)
-        for precision in ("fp32", "fp64"):
+        for precision in ("fp32", "fp64", "ff"):
             cases.append([f"N{n_fft}", dict(kw), precision, [None], 5])
     cases.append(["64s", dict(base="C1"), "fp32", _shapes(fc, sd.C1), 4])
     cases.append(["64s", dict(base="C1"), "fp64", [None], 3])
+    cases.append(["64s", dict(base="C1"), "ff", [None], 3])
     cases.append(["60min", dict(base="C2"), "fp32", [None], 2])
     return cases
 

@@ -12,7 +12,7 @@ from parity_util import RTOL, assert_parity, gpu_fitness, make_ctx, oracle_setup
 
 pytestmark = pytest.mark.gpu
 
-FORMS = ["fp32", "fp64"]
+FORMS = ["fp32", "fp64", "ff"]
 
 
 @pytest.fixture(scope="module", autouse=True)

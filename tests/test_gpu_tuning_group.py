@@ -114,7 +114,7 @@ def test_group_search_equals_individual_searches():
 def test_group_of_mixed_precisions_equals_individual_searches():
     import paper_2002_02150_gb300 as fc
     base = sd.SMALL
-    segs = [(base, "fp32"), (base, "fp64"), (dataclasses.replace(base, n_fft=8192, n_samples=6000), "fp64")]
+    segs = [(base, "fp32"), (base, "fp64"), (dataclasses.replace(base, n_fft=8192, n_samples=6000), "ff")]
     t0lo, t0hi, t15lo, t15hi = sd.chirp_time_box(base.f_low)
     box = (0.0, 2 * math.pi, -0.5 * math.pi, 0.5 * math.pi, t0lo, t0hi, t15lo, t15hi)
     cfg = fc.pso_config(n_runs=2, n_particles=8, n_iter=12, seed=11, box=box)

@@ -42,7 +42,7 @@ def _compare(w, precision, n):
             np.testing.assert_array_equal(t.cpu().numpy(), ref_t.cpu().numpy())
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("precision", ["fp32", "fp64", "ff"])
 def test_noalloc_matches_fitness_small(precision):
     _compare(sd.SMALL, precision, 37)
 
