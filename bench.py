@@ -43,7 +43,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=sd.C2.name)
-    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--fp64-steps", type=int, default=2,
+                    help="timed steps of the binary64 and float-float forms (0 = skip both)")
     ap.add_argument("--cpu-sample", type=int, default=1, help="particles per host core in the oracle CPU baseline")
     ap.add_argument("--particles", type=int, default=0, help="particles per GPU (0 = the workload's batch)")
     ap.add_argument("--max-batch", type=int, default=0, help="particles per internal chunk (0 = automatic)")
@@ -311,34 +312,46 @@ def bench_ours(args, ranks):
         cufft = bench_cufft(w, data, theta, *ref, dev, steps=args.cufft_batches)
         cufft["fp64"] = bench_cufft(w, data, theta, *ref, dev, steps=args.cufft_batches, fp64=True)
 
-    # plain binary64 form on the same workload (fewer steps: it is binary64-ALU bound)
-    fp64 = None
+    # plain binary64 form and the float-float form on the same workload (fewer steps: they are
+    # binary64- and FP32-issue bound)
+    fp64, ff = None, None
     if args.fp64_steps > 0:
         fit32, tc32 = fit.clone(), tc.clone()          # FP32-form results of the timed steps
-        ctx64 = fc.fcas_create(data["det"], data["psd"], data["data"], w.n_fft, w.fs, w.f_low, w.f_high,
-                               precision="fp64", max_batch=args.max_batch)
-        for _ in range(1):
-            fc.fcas_fitness(ctx64, th, fit, tc, stream=stream.cuda_stream)
-        ranks.barrier()
-        torch.cuda.synchronize(dev)
-        t0.record(stream)
-        for _ in range(args.fp64_steps):
-            fc.fcas_fitness(ctx64, th, fit, tc, stream=stream.cuda_stream)
-        t1.record(stream)
-        torch.cuda.synchronize(dev)
-        s64 = t0.elapsed_time(t1) / 1e3
-        v64, _ = aggregate(ranks, n * args.fp64_steps, s64)
-        tf64 = v64 * flop_per_eval(w.n_fft, info["n_det"], info["n_band"]) / 1e12
-        fp64 = {"value": round(v64, 2), "unit": UNIT, "steps": args.fp64_steps,
-                "ms_per_step": round(1e3 * s64 / args.fp64_steps, 3), "dtype": "f64",
-                "alu": {"bound": "alu", "achieved": round(tf64, 4), "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                        "frac": round(tf64 / FP64_NOMINAL_TFLOPS, 4), "peak_source": "nominal binary64 rate"}}
-        # error of the FP32 form (float-float phase) against the binary64 form on the same particles
-        rel = ((fit32 - fit).abs() / fit.abs()).double().cpu().numpy()
-        fp64["fp32_form_error"] = {"max_rel": float(rel.max()), "median_rel": float(np.median(rel)),
-                                   "same_tc_fraction": float((tc32 == tc).double().mean().item()),
-                                   "particles": n}
-        ctx64.close()
+        flop = flop_per_eval(w.n_fft, info["n_det"], info["n_band"])
+
+        def time_form(precision):
+            cx = fc.fcas_create(data["det"], data["psd"], data["data"], w.n_fft, w.fs, w.f_low, w.f_high,
+                                precision=precision, max_batch=args.max_batch)
+            fc.fcas_fitness(cx, th, fit, tc, stream=stream.cuda_stream)
+            ranks.barrier()
+            torch.cuda.synchronize(dev)
+            t0.record(stream)
+            for _ in range(args.fp64_steps):
+                fc.fcas_fitness(cx, th, fit, tc, stream=stream.cuda_stream)
+            t1.record(stream)
+            torch.cuda.synchronize(dev)
+            cx.close()
+            secs = t0.elapsed_time(t1) / 1e3
+            v, _ = aggregate(ranks, n * args.fp64_steps, secs)
+            return {"value": round(v, 2), "unit": UNIT, "steps": args.fp64_steps,
+                    "ms_per_step": round(1e3 * secs / args.fp64_steps, 3)}, v, fit.clone(), tc.clone()
+
+        def form_error(f_a, tc_a, f_ref, tc_ref):
+            rel = ((f_a - f_ref).abs() / f_ref.abs()).double().cpu().numpy()
+            return {"max_rel": float(rel.max()), "median_rel": float(np.median(rel)),
+                    "same_tc_fraction": float((tc_a == tc_ref).double().mean().item()), "particles": n}
+
+        fp64, v64, fit64, tc64 = time_form("fp64")
+        tf64 = v64 * flop / 1e12
+        fp64.update({"dtype": "f64",
+                     "alu": {"bound": "alu", "achieved": round(tf64, 4), "peak": FP64_NOMINAL_TFLOPS,
+                             "unit": "TFLOP/s", "frac": round(tf64 / FP64_NOMINAL_TFLOPS, 4),
+                             "peak_source": "nominal binary64 rate"},
+                     # error of the FP32 form (float-float phase) against the binary64 form
+                     "fp32_form_error": form_error(fit32, tc32, fit64, tc64)})
+        ff, _, fitff, tcff = time_form("ff")
+        ff.update({"dtype": "f64 phase + float-float transforms",
+                   "error_vs_fp64_form": form_error(fitff, tcff, fit64, tc64)})
 
     search = None if args.no_search else bench_search(fc, ranks, data, w, dev)
     group = None if args.group_segments <= 0 else bench_group(fc, ranks, args.group_segments, dev)
@@ -364,7 +377,7 @@ def bench_ours(args, ranks):
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
                      "note": "whole fitness path per GPU; both passes issue-bound (see profiles/)"},
         "kernels": kernels, "gpu_launches": gpu_launches, "e2e": e2e, "clocks": clock,
-        "fp64_form": fp64, "cufft_form": cufft,
+        "fp64_form": fp64, "ff_form": ff, "cufft_form": cufft,
         "search_time_over_data_time": (search["search_time_over_data_time"] if search else
                                        {"value": round(PSO_EVALS / value / DATA_SECONDS, 5),
                                         "how": "extrapolated: 8 runs x 40 particles x 2000 iterations / value / 3600 s"}),
