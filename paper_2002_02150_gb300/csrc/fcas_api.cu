@@ -72,7 +72,7 @@ namespace {
 void free_ctx(fcas_ctx* c) {
     void* ptrs[] = {c->d_det, c->d_sigma2s, c->d_y, c->d_basis, c->d_tw64, c->d_twlo64, c->d_twhi64,
                     c->d_tw32, c->d_twlo32, c->d_twhi32, c->d_stw_a64, c->d_stw_a32, c->d_stw_b64, c->d_stw_b32,
-                    c->d_twloff, c->d_twhiff, c->d_stw_aff, c->d_stw_bff,
+                    c->d_twloff, c->d_twhiff, c->d_stw_aff, c->d_stw_bff, c->d_phff,
                     c->d_params, c->d_theta, c->d_fit, c->d_tc, c->d_inter, c->d_partials, c->d_pso,
                     c->d_gsums, c->d_gstage, c->d_ynat};
     for (void* p : ptrs)
@@ -426,6 +426,8 @@ int create_impl(fcas_ctx** out, const fcas_setup* setup, const fcas_detector* de
         FCAS_TRY(dev_alloc(&c->d_stw_bff, sizeof(double2) << kMaxLogPass, "float-float stage twiddles"));
         FCAS_TRYCUDA(launch_split_ff(c->d_twlo64, c->d_twloff, (int64_t)nlo, st));
         FCAS_TRYCUDA(launch_split_ff(c->d_twhi64, c->d_twhiff, (int64_t)nhi, st));
+        FCAS_TRY(dev_alloc(&c->d_phff, sizeof(double2) * 1024, "float-float phasor table"));
+        FCAS_TRYCUDA(launch_phase_table_ff(c->d_phff, 1024, st));
     }
 
     // forward FFT of the data (binary64) and the whitened, re-laid-out band spectrum
@@ -973,7 +975,8 @@ int fcas_gradient(fcas_ctx* c, int64_t n, const double* theta, const int64_t* tc
     if (c->setup.precision == FCAS_PREC_FP32)
         FCAS_CUDA(launch_grad_sums<float>(plan, k1b, c->k_lo, c->k_hi, c->d_params, d_tc, n, c->d_gsums, st));
     else
-        FCAS_CUDA(launch_grad_sums<double>(plan, k1b, c->k_lo, c->k_hi, c->d_params, d_tc, n, c->d_gsums, st));
+        FCAS_CUDA(launch_grad_sums<double>(plan, k1b, c->k_lo, c->k_hi, c->d_params, d_tc, n, c->d_gsums, st,
+                                           c->setup.precision == FCAS_PREC_FF));
     FCAS_CUDA(launch_grad_final(d_theta, d_tc, n, c->d_gsums, c->d_det, c->d_sigma2s, c->setup.n_det, c->setup.f_low,
                                 c->df, d_grad, st));
     if (!g_dev) {

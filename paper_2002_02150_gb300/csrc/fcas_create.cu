@@ -86,6 +86,21 @@ __global__ void split_ff_kernel(const double2* __restrict__ src, float4* __restr
     }
 }
 
+__global__ void phase_table_ff_kernel(float4* __restrict__ dst, int n) {
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n; m += gridDim.x * blockDim.x) {
+        double sn, cs;
+        sincospi(2.0 * (double)m / (double)n, &sn, &cs);
+        const float xh = (float)cs, yh = (float)sn;
+        dst[m] = make_float4(xh, (float)(cs - (double)xh), yh, (float)(sn - (double)yh));
+    }
+}
+
+cudaError_t launch_phase_table_ff(void* dst, int n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    phase_table_ff_kernel<<<(n + 255) / 256, 256, 0, s>>>(static_cast<float4*>(dst), n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_split_ff(const double2* src, void* dst, int64_t n, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     int64_t blocks = (n + 255) / 256;
@@ -311,7 +326,7 @@ cudaError_t launch_whiten(const double2* spec, const double* psd, int n_det, int
 
 // ------------------------------------------------------------------------------------------
 // Layout of the spectrum for pass A: Y as [k1 / K1B][i][k2 < N2/2][k1 % K1B] with k = k1 + N1 k2 (one
-// detector's rows of a block adjacent), and the chirp basis phi^-5/3, phi^-1, phi^-2/3, phi^-1/3
+// detector's rows of a block adjacent; float pairs, binary64 pairs or float-float quadruples), and the chirp basis phi^-5/3, phi^-1, phi^-2/3, phi^-1/3
 // (phi = f_k / f_*) in the order [k1 / K1B][k2][k1 % K1B] (float-float pairs in the FP32 form).
 // ------------------------------------------------------------------------------------------
 __global__ void layout_kernel(const double2* __restrict__ ynat, int n_det, int log_n, int log_n1, int log_n2, int k1b,
@@ -331,8 +346,14 @@ __global__ void layout_kernel(const double2* __restrict__ ynat, int n_det, int l
         for (int i = 0; i < n_det; ++i) {
             const double2 yv = ynat[(int64_t)i * half + k];
             const int64_t yi = ((blk * n_det + i) * half2 + k2) * k1b + c;
-            if (precision == FCAS_PREC_FP32) static_cast<float2*>(y)[yi] = make_float2((float)yv.x, (float)yv.y);
-            else static_cast<double2*>(y)[yi] = yv;
+            if (precision == FCAS_PREC_FP32) {
+                static_cast<float2*>(y)[yi] = make_float2((float)yv.x, (float)yv.y);
+            } else if (precision == FCAS_PREC_FF) {
+                const float xh = (float)yv.x, ih = (float)yv.y;
+                static_cast<float4*>(y)[yi] = make_float4(xh, (float)(yv.x - (double)xh), ih, (float)(yv.y - (double)ih));
+            } else {
+                static_cast<double2*>(y)[yi] = yv;
+            }
         }
         double b53 = 0.0, b1 = 0.0, b23 = 0.0, b13 = 0.0;
         if (k >= k_lo && k <= k_hi) {

@@ -58,6 +58,7 @@ struct fcas_ctx {
     void* d_twhiff = nullptr;       // stage tables (FCAS_PREC_FF contexts only)
     void* d_stw_aff = nullptr;
     void* d_stw_bff = nullptr;
+    void* d_phff = nullptr;         // float-float phasor table e^{2 pi i m / 1024} (FCAS_PREC_FF contexts only)
     fcas::ParticleParams* d_params = nullptr;
     int64_t params_cap = 0;
     double* d_theta = nullptr;      // staging for host theta
@@ -116,6 +117,7 @@ inline FitnessPlan make_plan(const fcas_ctx* c) {
     p.sub = c->sub;
     p.tw_lo = ff ? c->d_twloff : c->d_twlo;
     p.tw_hi = ff ? c->d_twhiff : c->d_twhi;
+    p.ptab = c->d_phff;
     return p;
 }
 

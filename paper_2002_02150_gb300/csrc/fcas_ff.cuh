@@ -43,6 +43,15 @@ __device__ __forceinline__ ffloat ff_add(ffloat a, ffloat b) {
     const float hi = ff_fast_two_sum(s, e, lo);
     return ffloat(hi, lo);
 }
+// a + b for a float b (the same sum with a zero low part of b)
+__device__ __forceinline__ ffloat ff_add_f(ffloat a, float b) {
+    float e;
+    const float s = ff_two_sum(a.h, b, e);
+    e = __fadd_rn(e, a.l);
+    float lo;
+    const float hi = ff_fast_two_sum(s, e, lo);
+    return ffloat(hi, lo);
+}
 __device__ __forceinline__ ffloat ff_neg(ffloat a) { return ffloat(-a.h, -a.l); }
 __device__ __forceinline__ ffloat ff_sub(ffloat a, ffloat b) { return ff_add(a, ff_neg(b)); }
 // a b: the exact leading product by a fused multiply-add plus the cross terms (double-word product)

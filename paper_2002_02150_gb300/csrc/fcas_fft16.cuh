@@ -18,6 +18,8 @@
 // so that a warp reads consecutive entries; the stages together use L - 1 entries.
 #pragma once
 
+#include <type_traits>
+
 #include "fcas_internal.cuh"
 #include "fcas_ff.cuh"
 
@@ -210,8 +212,10 @@ __device__ __forceinline__ void fftr_stage(cplx<Real> (&v)[fftr_v(LOG_L, MAXRB)]
         if constexpr (NS > 1) {
             const int jm = jj & (NS - 1);
             const C* t = stw + (NS - 1) + jm;
-            if constexpr (R >= 8) {
-                // w^r for r = 1..R-1 from two table entries: w and w^4 (powers by products, <= 3 roundings)
+            if constexpr (R >= 8 && !std::is_same<Real, ffloat>::value) {
+                // w^r for r = 1..R-1 from two table entries: w and w^4 (powers by products, <= 3 roundings);
+                // the float-float form loads every power instead (a double-word product costs more
+                // than a load)
                 C w1 = mkc((Real)1, (Real)0), w4 = w1;
                 if (FCAS_CHECK((NS - 1) + jm + 3 * NS < L, kCheckTwiddle)) {
                     w1 = ldg_c(t);

@@ -27,7 +27,7 @@ __device__ __forceinline__ float frac_mul_ff_g(float ah, float al, float bh, flo
 
 template <typename Real>
 __global__ void __launch_bounds__(256)
-grad_sums_kernel(const cplx<Real>* __restrict__ y, const Basis<Real>* __restrict__ basis,
+grad_sums_kernel(const cplx<Real>* __restrict__ y, bool y_ff, const Basis<Real>* __restrict__ basis,
                  const ParticleParams* __restrict__ params, const int64_t* __restrict__ tc, int n_det, int log_n,
                  int log_n1, int log_n2, int k1b, int64_t k_lo, int64_t k_hi, double* __restrict__ sums) {
     __shared__ double red[kGradSums][8];
@@ -45,7 +45,17 @@ grad_sums_kernel(const cplx<Real>* __restrict__ y, const Basis<Real>* __restrict
             const int64_t blk = g / per_blk, rem = g % per_blk;
             const int64_t k = blk * k1b + rem % k1b + n1 * (rem / k1b);
             if (k < k_lo || k > k_hi) continue;
-            const cplx<Real> yv = y[(blk * n_det + i) * per_blk + rem];
+            cplx<Real> yv;
+            if constexpr (sizeof(Real) == 8) {
+                if (y_ff) {   // float-float layout (FCAS_PREC_FF contexts): 16-byte entries hi/lo re, hi/lo im
+                    const float4 q = reinterpret_cast<const float4*>(y)[(blk * n_det + i) * per_blk + rem];
+                    yv = make_double2((double)q.x + (double)q.y, (double)q.z + (double)q.w);
+                } else {
+                    yv = y[(blk * n_det + i) * per_blk + rem];
+                }
+            } else {
+                yv = y[(blk * n_det + i) * per_blk + rem];
+            }
             const Basis<Real> b = basis[g];
             const double shift = (double)((k * t) & (n - 1)) / (double)n;   // k t / N mod 1, exact
             double qr, qi, b53, b1, b23, b13;
@@ -247,10 +257,10 @@ __global__ void grad_final_kernel(const double* __restrict__ theta, const int64_
 
 template <typename Real>
 cudaError_t launch_grad_sums(const FitnessPlan& pl, int k1b, int64_t k_lo, int64_t k_hi, const ParticleParams* params,
-                             const int64_t* tc, int64_t n, double* sums, cudaStream_t s) {
+                             const int64_t* tc, int64_t n, double* sums, cudaStream_t s, bool y_ff) {
     if (n <= 0) return cudaSuccess;
     dim3 grid((unsigned)n, (unsigned)pl.n_det);
-    grad_sums_kernel<Real><<<grid, 256, 0, s>>>(static_cast<const cplx<Real>*>(pl.y),
+    grad_sums_kernel<Real><<<grid, 256, 0, s>>>(static_cast<const cplx<Real>*>(pl.y), y_ff,
                                                 static_cast<const Basis<Real>*>(pl.basis), params, tc, pl.n_det,
                                                 pl.log_n, pl.log_n1, pl.log_n2, k1b, k_lo, k_hi, sums);
     return cudaGetLastError();
@@ -265,8 +275,8 @@ cudaError_t launch_grad_final(const double* theta, const int64_t* tc, int64_t n,
 }
 
 template cudaError_t launch_grad_sums<float>(const FitnessPlan&, int, int64_t, int64_t, const ParticleParams*,
-                                             const int64_t*, int64_t, double*, cudaStream_t);
+                                             const int64_t*, int64_t, double*, cudaStream_t, bool);
 template cudaError_t launch_grad_sums<double>(const FitnessPlan&, int, int64_t, int64_t, const ParticleParams*,
-                                              const int64_t*, int64_t, double*, cudaStream_t);
+                                              const int64_t*, int64_t, double*, cudaStream_t, bool);
 
 }  // namespace fcas

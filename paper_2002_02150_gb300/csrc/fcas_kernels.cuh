@@ -72,6 +72,7 @@ struct FitnessPlan {
     int sub;                      // adjacent column blocks of a particle scheduled together
     const void* tw_lo;            // e^{2 pi i m / N}, m < 4096
     const void* tw_hi;            // e^{2 pi i 4096 m / N}, m < max(1, N / 4096)
+    const void* ptab;             // float-float e^{2 pi i m / 1024}, m < 1024 (FCAS_PREC_FF only)
 };
 
 // Per-particle geometry (binary64): chirp coefficients, delays, antenna patterns, G^-1.
@@ -97,6 +98,8 @@ int pass_b_blocks_per_particle(int log_n1, int log_n2, int precision);
 unsigned int take_index_checks(cudaStream_t s);
 // float-float copy (16-byte entries: hi/lo of re, hi/lo of im) of a binary64 complex table
 cudaError_t launch_split_ff(const double2* src, void* dst, int64_t n, cudaStream_t s);
+// float-float table of e^{2 pi i m / n}, m < n (16-byte entries as above)
+cudaError_t launch_phase_table_ff(void* dst, int n, cudaStream_t s);
 unsigned int take_index_checks_ff(cudaStream_t s);   // the float-float passes' translation unit
 int pass_a_k1b_for(int log_n2, int precision);
 // compiled pass-A column-block widths for a length: writes up to 3 values, returns the count
@@ -108,7 +111,7 @@ bool pass_a_radix8_available(int log_n2, int precision, int k1b);
 // ---- adjoint (fcas_grad.cu) ----
 template <typename Real>
 cudaError_t launch_grad_sums(const FitnessPlan& pl, int k1b, int64_t k_lo, int64_t k_hi, const ParticleParams* params,
-                             const int64_t* tc, int64_t n, double* sums, cudaStream_t s);
+                             const int64_t* tc, int64_t n, double* sums, cudaStream_t s, bool y_ff = false);
 cudaError_t launch_grad_final(const double* theta, const int64_t* tc, int64_t n, const double* sums,
                               const double* det9, const double* s2, int n_det, double f_star, double df, double* grad,
                               cudaStream_t s);

@@ -63,6 +63,37 @@ __device__ __forceinline__ double2 unit_phasor(double turns) {
     return make_double2(cs, sn);
 }
 
+// Entries of the float-float phasor table: e^{2 pi i m / kPhaseTab}, m < kPhaseTab.
+constexpr int kPhaseTabBits = 10;
+constexpr int kPhaseTab = 1 << kPhaseTabBits;
+
+// e^{2 pi i u} in float-float for |u| <= 1/2 given in binary64, on the FP32 units (table-driven
+// reduction in the manner of Tang 1990): u = m / 1024 + r with the nearest table point m, and
+// e^{2 pi i u} = T[m] (cos x + i sin x), x = 2 pi r, |x| <= pi / 1024. The remainder is exact in
+// float-float (u split into two floats, the table point subtracted exactly by a fused multiply-add);
+// sin x = x - x^3/6 + x^5/120 and cos x = 1 - x^2/2 + x^4/24 (Taylor; the first omitted terms are
+// below 2e-18), with x and x^2 in float-float and the small terms in float. Absolute error a few
+// units of 2^-48.
+__device__ __forceinline__ ff2 ff_unit_phasor(double u, const ff2* __restrict__ tab) {
+    const float uh = __double2float_rn(u);
+    const float ul = __double2float_rn(u - (double)uh);
+    const float m = rintf(uh * (float)kPhaseTab);
+    float rl;
+    const float rh = ff_two_sum(__fmaf_rn(m, -1.0f / (float)kPhaseTab, uh), ul, rl);
+    const ffloat x = ff_mul(ffloat(rh, rl), ffloat(6.28318548202514648f, -1.74845553146951557e-7f));
+    const ffloat x2 = ff_mul(x, x);
+    // cos x = 1 - (x^2/2 - x^4/24)
+    const ffloat hc = ff_add_f(ffloat(0.5f * x2.h, 0.5f * x2.l), -(x2.h * x2.h) * (1.0f / 24.0f));
+    float e;
+    const float ch = ff_fast_two_sum(1.0f, -hc.h, e);
+    float cl;
+    const float c = ff_fast_two_sum(ch, __fsub_rn(e, hc.l), cl);
+    // sin x = x - x^3/6 (1 - x^2/20)
+    const ffloat sn = ff_add_f(x, -(x.h * x2.h) * (1.0f / 6.0f) * __fmaf_rn(x2.h, -0.05f, 1.0f));
+    const ff2 t = ldg_c(tab + ((int)m & (kPhaseTab - 1)));
+    return cmul(t, ff2{ffloat(c, cl), sn});
+}
+
 // ------------------------------------------------------------------------------------------
 // Pass A: for every band bin of the CTA's columns, Q_i[k] = Y_i[k] e^{2 pi i (psi(f_k)/2pi + f_k Delta^i)}
 // is generated on the load and combined over detectors into the two network-weighted spectra
@@ -77,16 +108,11 @@ __host__ __device__ constexpr bool pass_a_pingpong() {
     return 2 * sizeof(cplx<Real>) * (size_t)K1B * fft16_buf_elems(LOG_L) <= 200 * 1024;
 }
 
-// The float-float form generates the phase in binary64 (spectrum, basis, delays and chirp as in the
-// binary64 form) and converts the two detector sums to float-float before the transforms.
+// The float-float form reduces the chirp and delay phases in binary64 (basis and delays as in the
+// binary64 form) and forms the phasors, the detector sums and everything after them in float-float.
 template <typename Real> struct phase_of { using type = Real; };
 template <> struct phase_of<ffloat> { using type = double; };
 template <typename Real> using phase_t = typename phase_of<Real>::type;
-
-template <typename Real> __device__ __forceinline__ cplx<Real> to_real_c(cplx<phase_t<Real>> v) {
-    if constexpr (std::is_same<Real, ffloat>::value) return ff2{ffloat(v.x), ffloat(v.y)};
-    else return v;
-}
 
 // streamed store (evict-first): the intermediate is read back only by pass B
 __device__ __forceinline__ void st_stream(float2* p, float2 v) { __stcs(p, v); }
@@ -97,25 +123,27 @@ __device__ __forceinline__ void st_stream(ff2* p, ff2 v) {
 
 template <typename Real>
 struct DetConst {
-    Real dh[FCAS_MAX_DET], dl[FCAS_MAX_DET], w1[FCAS_MAX_DET], w2[FCAS_MAX_DET];
+    phase_t<Real> dh[FCAS_MAX_DET], dl[FCAS_MAX_DET];
+    Real w1[FCAS_MAX_DET], w2[FCAS_MAX_DET];
 };
 
 template <typename Real, int LOG_L, int K1B, int MAXRB>
 __global__ void __launch_bounds__(K1B * ((1 << LOG_L) / fftr_v(LOG_L, MAXRB)), 1)
-pass_a_kernel(const cplx<phase_t<Real>>* __restrict__ y, const Basis<phase_t<Real>>* __restrict__ basis,
+pass_a_kernel(const cplx<Real>* __restrict__ y, const Basis<phase_t<Real>>* __restrict__ basis,
               const ParticleParams* __restrict__ params, int64_t p0, int64_t np, int n_det, int log_n1, int sub_req,
               cplx<Real>* __restrict__ out, const cplx<Real>* __restrict__ stw,
-              const cplx<Real>* __restrict__ tw_lo, const cplx<Real>* __restrict__ tw_hi) {
+              const cplx<Real>* __restrict__ tw_lo, const cplx<Real>* __restrict__ tw_hi,
+              const cplx<Real>* __restrict__ ptab) {
     using C = cplx<Real>;
-    using P = phase_t<Real>;      // the real type of the phase generation (binary64 for the float-float form)
-    using CP = cplx<P>;
+    using P = phase_t<Real>;      // the real type of the phase reduction (binary64 for the float-float form)
+    constexpr bool kFF = std::is_same<Real, ffloat>::value;
     constexpr int L = 1 << LOG_L;
     constexpr int V = fftr_v(LOG_L, MAXRB);
     constexpr int G = L / V;
     constexpr int VH = V / 2;    // values with k2 < L/2; the rest of the column is zero (k >= N/2)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* smem = reinterpret_cast<C*>(smem_raw);
-    __shared__ DetConst<P> sc;
+    __shared__ DetConst<Real> sc;
 
     const int c = threadIdx.x % K1B;
     const int j = threadIdx.x / K1B;
@@ -142,8 +170,8 @@ pass_a_kernel(const cplx<phase_t<Real>>* __restrict__ y, const Basis<phase_t<Rea
         } else {
             sc.dh[i] = pp->dturn[i];
             sc.dl[i] = 0.0;
-            sc.w1[i] = pp->w1[i];
-            sc.w2[i] = pp->w2[i];
+            sc.w1[i] = Real(pp->w1[i]);
+            sc.w2[i] = Real(pp->w2[i]);
         }
     }
     __syncthreads();
@@ -153,9 +181,9 @@ pass_a_kernel(const cplx<phase_t<Real>>* __restrict__ y, const Basis<phase_t<Rea
     // of consecutive q differ by the constant factor e^{2 pi i N1 G Delta^i / T}: one accurate phasor
     // and one step per detector, then products. The chirp phasor multiplies the detector sums last:
     // P_a[k] = e^{i psi(f_k)} sum_i w_a,i Y_i[k] e^{2 pi i f_k Delta^i}.
-    CP r1[VH], r2[VH];
+    C r1[VH], r2[VH];
 #pragma unroll
-    for (int q = 0; q < VH; ++q) r1[q] = r2[q] = mkc((P)0, (P)0);
+    for (int q = 0; q < VH; ++q) r1[q] = r2[q] = mkc(Real(0.0f), Real(0.0f));
     // the chirp basis of the thread's bins is requested first: its latency overlaps the detector sums
     const Basis<P>* bb = basis + ((int64_t)blk * (L / 2) + j) * K1B + c;
     Basis<P> bq[sizeof(P) == 4 ? VH : 1];
@@ -169,10 +197,25 @@ pass_a_kernel(const cplx<phase_t<Real>>* __restrict__ y, const Basis<phase_t<Rea
     const int kbase = k1 + n1 * j;
     const int kstep = n1 * G;
     const int64_t col0 = (int64_t)blk * n_det;
-#pragma unroll
+    // The float-float form keeps its code small (its fully unrolled double-word arithmetic would not
+    // fit the instruction cache): the chirp phasors are formed in a loop into shared memory (the
+    // transforms' exchange buffers, not yet in use) and the detector loop is not unrolled.
+    if constexpr (kFF) {
+#pragma unroll 1
+        for (int q = 0; q < VH; ++q) {
+            Basis<P> b{};
+            if (FCAS_CHECK(((int64_t)blk * (L / 2) + j) * K1B + c + (int64_t)q * G * K1B < ((int64_t)L / 2 << log_n1),
+                           kCheckBasis))
+                b = bb[(int64_t)q * G * K1B];
+            if (FCAS_CHECK(q * (int)blockDim.x + (int)threadIdx.x < K1B * fft16_buf_elems(LOG_L), kCheckExchangeWrite))
+                smem[q * blockDim.x + threadIdx.x] = ff_unit_phasor(chirp_frac(b, *pp), ptab);
+        }
+    }
+    constexpr int kDetUnroll = kFF ? 1 : FCAS_MAX_DET;
+#pragma unroll kDetUnroll
     for (int i = 0; i < FCAS_MAX_DET; ++i) {
         if (i >= n_det) break;
-        CP dph, dstep;
+        C dph, dstep;
         if constexpr (sizeof(P) == 4) {
             float fb = frac_mul_ff((float)kbase, 0.0f, sc.dh[i], sc.dl[i]);
             float fs = frac_mul_ff((float)kstep, 0.0f, sc.dh[i], sc.dl[i]);
@@ -182,18 +225,25 @@ pass_a_kernel(const cplx<phase_t<Real>>* __restrict__ y, const Basis<phase_t<Rea
             dstep = fast_phasor(fs);
         } else {
             double fb = (double)kbase * sc.dh[i], fs = (double)kstep * sc.dh[i];
-            dph = unit_phasor(fb - rint(fb));
-            dstep = unit_phasor(fs - rint(fs));
+            if constexpr (kFF) {
+                dph = ff_unit_phasor(fb - rint(fb), ptab);
+                dstep = ff_unit_phasor(fs - rint(fs), ptab);
+            } else {
+                dph = unit_phasor(fb - rint(fb));
+                dstep = unit_phasor(fs - rint(fs));
+            }
         }
-        const CP* yd = y + ((col0 + i) * (L / 2) + j) * K1B + c;
-        const P w1 = sc.w1[i], w2 = sc.w2[i];
+        const C* yd = y + ((col0 + i) * (L / 2) + j) * K1B + c;
+        const Real w1 = sc.w1[i], w2 = sc.w2[i];
 #pragma unroll
         for (int q = 0; q < VH; ++q) {
-            CP yv = mkc((P)0, (P)0);
+            C yv = mkc(Real(0.0f), Real(0.0f));
             if (FCAS_CHECK(((col0 + i) * (L / 2) + j) * K1B + c + (int64_t)q * G * K1B <
-                               (int64_t)n_det * ((int64_t)L / 2 << log_n1), kCheckSpectrum))
-                yv = yd[(int64_t)q * G * K1B];
-            const CP t = cmul(yv, dph);
+                               (int64_t)n_det * ((int64_t)L / 2 << log_n1), kCheckSpectrum)) {
+                if constexpr (kFF) yv = ldg_c(yd + (int64_t)q * G * K1B);
+                else yv = yd[(int64_t)q * G * K1B];
+            }
+            const C t = cmul(yv, dph);
             r1[q].x += w1 * t.x;
             r1[q].y += w1 * t.y;
             r2[q].x += w2 * t.x;
@@ -212,7 +262,7 @@ pass_a_kernel(const cplx<phase_t<Real>>* __restrict__ y, const Basis<phase_t<Rea
         }
 #pragma unroll
         for (int q = 0; q < VH; ++q) {
-            CP cp;
+            C cp;
             if constexpr (sizeof(P) == 4) {
                 const ChirpPowers b = chirp_powers(bq[q]);
                 float s = frac_mul_ff(cfh[0], cfl[0], b.b53.x, b.b53.y);
@@ -220,6 +270,8 @@ pass_a_kernel(const cplx<phase_t<Real>>* __restrict__ y, const Basis<phase_t<Rea
                 s += frac_mul_ff(cfh[2], cfl[2], b.b23.x, b.b23.y);
                 s += frac_mul_ff(cfh[3], cfl[3], b.b13.x, b.b13.y);
                 cp = fast_phasor(s - rintf(s));
+            } else if constexpr (kFF) {
+                cp = smem[q * blockDim.x + threadIdx.x];
             } else {
                 Basis<P> b{};
                 if (FCAS_CHECK(((int64_t)blk * (L / 2) + j) * K1B + c + (int64_t)q * G * K1B <
@@ -231,14 +283,15 @@ pass_a_kernel(const cplx<phase_t<Real>>* __restrict__ y, const Basis<phase_t<Rea
             r2[q] = cmul(r2[q], cp);
         }
     }
+    if constexpr (kFF) __syncthreads();   // every chirp phasor read before the exchange buffers are reused
 
 #pragma unroll 1
     for (int a = 0; a < kSeries; ++a) {
         C v[V];
 #pragma unroll
-        for (int q = 0; q < VH; ++q) v[q] = to_real_c<Real>(a == 0 ? r1[q] : r2[q]);
+        for (int q = 0; q < VH; ++q) v[q] = a == 0 ? r1[q] : r2[q];
 #pragma unroll
-        for (int q = VH; q < V; ++q) v[q] = mkc((Real)0, (Real)0);
+        for (int q = VH; q < V; ++q) v[q] = mkc(Real(0.0f), Real(0.0f));
         // two exchange buffers where shared memory allows (no barrier before each exchange write); the
         // exchange count is continued across the series so that a buffer is never rewritten before
         // all its reads of the previous exchange are done
@@ -367,11 +420,11 @@ static cudaError_t pass_a_at(const FitnessPlan& pl, const ParticleParams* params
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t ctas = np * ((1 << pl.log_n1) / K1B);
-    kern<<<(unsigned)ctas, THREADS, smem, s>>>(static_cast<const cplx<phase_t<Real>>*>(pl.y),
+    kern<<<(unsigned)ctas, THREADS, smem, s>>>(static_cast<const cplx<Real>*>(pl.y),
                                      static_cast<const Basis<phase_t<Real>>*>(pl.basis),
                                      params, p0, np, pl.n_det, pl.log_n1, pl.sub, static_cast<cplx<Real>*>(inter),
                                      static_cast<const cplx<Real>*>(pl.stw_a), static_cast<const cplx<Real>*>(pl.tw_lo),
-                                     static_cast<const cplx<Real>*>(pl.tw_hi));
+                                     static_cast<const cplx<Real>*>(pl.tw_hi), static_cast<const cplx<Real>*>(pl.ptab));
     return cudaGetLastError();
 }
 

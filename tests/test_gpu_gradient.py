@@ -10,7 +10,7 @@ from parity_util import make_ctx, oracle_setup
 
 pytestmark = pytest.mark.gpu
 
-GRAD_RTOL = {"fp32": 2e-3, "fp64": 1e-8}
+GRAD_RTOL = {"fp32": 2e-3, "fp64": 1e-8, "ff": 1e-8}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -37,7 +37,7 @@ def _check(setup, theta, tc, g, precision, context):
         assert err <= GRAD_RTOL[precision] * scale, f"{context} particle {j}: {g[j]} vs {ref}"
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("precision", ["fp32", "fp64", "ff"])
 def test_gradient_matches_oracle_small(precision):
     w = sd.SMALL
     data = sd.make_dataset(w, 7)
