@@ -202,8 +202,11 @@ int apply_layout(fcas_ctx* c, int bias, int k1b, int sub, int radix_bits_a, cuda
     if (nk <= 0) return fail(FCAS_ERR_INVALID, "no pass-A shape for 2^%d-point columns", l2);
     if (k1b == 0) k1b = ks[0];
     bool ok = false;
-    for (int q = 0; q < nk; ++q) ok |= ks[q] == k1b;
-    if (!ok) return fail(FCAS_ERR_INVALID, "pass-A width %d not compiled for 2^%d-point columns", k1b, l2);
+    if (radix_bits_a == 3) ok = pass_a_radix8_available(l2, c->setup.precision, k1b);
+    else for (int q = 0; q < nk; ++q) ok |= ks[q] == k1b;
+    if (!ok)
+        return fail(FCAS_ERR_INVALID, "pass-A width %d with radix bits %d not compiled for 2^%d-point columns", k1b,
+                    radix_bits_a, l2);
     if (sub < 1 || (sub & (sub - 1))) return fail(FCAS_ERR_INVALID, "CTA grouping %d is not a power of two", sub);
     if (radix_bits_a != 4 && !(radix_bits_a == 3 && pass_a_radix8_available(l2, c->setup.precision, k1b)))
         return fail(FCAS_ERR_INVALID, "pass-A radix %d not compiled for this shape", 1 << radix_bits_a);
@@ -446,7 +449,8 @@ int create_impl(fcas_ctx** out, const fcas_setup* setup, const fcas_detector* de
     FCAS_TRY(dev_alloc(&c->d_stw_a32, sizeof(float2) << kMaxLogPass, "stage twiddles"));
     FCAS_TRY(dev_alloc(&c->d_stw_b64, sizeof(double2) << kMaxLogPass, "stage twiddles"));
     FCAS_TRY(dev_alloc(&c->d_stw_b32, sizeof(float2) << kMaxLogPass, "stage twiddles"));
-    FCAS_TRY(apply_layout(c, FCAS_SPLIT_BIAS, 0, FCAS_PASS_A_SUB, 4, st));
+    FCAS_TRY(apply_layout(c, FCAS_SPLIT_BIAS, 0, FCAS_PASS_A_SUB,
+                          pass_a_default_radix_bits(split_log_n2_with(c->log_n, FCAS_SPLIT_BIAS), s.precision), st));
 
     // scratch for the fitness path (partials sized for every split the tuner may choose)
     const size_t per_particle = inter_bytes_per_particle(s.precision, n);
@@ -710,12 +714,14 @@ int fcas_autotune(fcas_ctx* c, int64_t n_particles, const char* cache_path, void
         const int l2 = split_log_n2_with(c->log_n, bias);
         if (l2 == last_l2 || c->log_n - l2 > kMaxLogPass) continue;
         last_l2 = l2;
-        int ks[3], rbs[4];
-        int nk = pass_a_k1b_variants(l2, c->setup.precision, ks);
+        int ks[5], rbs[5];
+        int nk = pass_a_k1b_variants(l2, c->setup.precision, ks);   // at most 3
         for (int q = 0; q < nk; ++q) rbs[q] = 4;
-        if (pass_a_radix8_available(l2, c->setup.precision, 4)) {
-            ks[nk] = 4;
-            rbs[nk++] = 3;
+        for (int k8 : {4, 2}) {
+            if (pass_a_radix8_available(l2, c->setup.precision, k8)) {
+                ks[nk] = k8;
+                rbs[nk++] = 3;
+            }
         }
         for (int q = 0; q < nk && rc == FCAS_OK; ++q) {
             for (int si = 0; si < 4 && rc == FCAS_OK; ++si) {
@@ -765,7 +771,9 @@ int fcas_set_shape(fcas_ctx* c, int32_t split_bias, int32_t k1b, int32_t sub, in
     if (!c) return fail(FCAS_ERR_INVALID, "fcas_set_shape: NULL context");
     if (split_bias < 0 || split_bias > 1) return fail(FCAS_ERR_INVALID, "fcas_set_shape: split_bias must be 0 or 1");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    int rc = apply_layout(c, split_bias, k1b, sub, radix_bits_a == 0 ? 4 : radix_bits_a, st);
+    if (radix_bits_a == 0) radix_bits_a = pass_a_default_radix_bits(split_log_n2_with(c->log_n, split_bias),
+                                                                     c->setup.precision);
+    int rc = apply_layout(c, split_bias, k1b, sub, radix_bits_a, st);
     if (rc) return rc;
     c->tuned_ms = 0.0;
     FCAS_CUDA(cudaStreamSynchronize(st));

@@ -183,7 +183,13 @@ int pass_b_blocks_per_particle(int log_n1, int log_n2, int precision) {
 }
 
 bool pass_a_radix8_available(int log_n2, int precision, int k1b) {
-    return precision == FCAS_PREC_FP32 && log_n2 >= 10 && log_n2 <= 12 && k1b == 4;
+    return log_n2 >= 10 && log_n2 <= 12 &&
+           ((precision == FCAS_PREC_FP32 && k1b == 4) || (precision == FCAS_PREC_FF && k1b == 2));
+}
+
+int pass_a_default_radix_bits(int log_n2, int precision) {
+    // float-float: radix 8 halves the registers per thread (16 resident warps per SM instead of 8)
+    return precision == FCAS_PREC_FF && log_n2 == 11 ? 3 : 4;
 }
 
 int pass_a_k1b_variants(int log_n2, int precision, int* out) {

@@ -107,6 +107,8 @@ int pass_a_k1b_variants(int log_n2, int precision, int* out);
 cudaError_t launch_stage_tables(int log_l, int maxrb, double2* t64, float2* t32, cudaStream_t s);
 // pass A with radix-8 stages (8 values per thread) is compiled for these shapes
 bool pass_a_radix8_available(int log_n2, int precision, int k1b);
+// pass-A stage radix bits a context starts with (and fcas_set_shape's radix_bits_a = 0)
+int pass_a_default_radix_bits(int log_n2, int precision);
 
 // ---- adjoint (fcas_grad.cu) ----
 template <typename Real>

@@ -444,6 +444,9 @@ static cudaError_t pass_a_lg(const FitnessPlan& pl, const ParticleParams* params
         // radix-8 stages: 8 values per thread, 1024-thread CTAs of 4 columns (FP32, >= 2^10 points)
         if constexpr (RB == 4 && LG >= 10 && LG <= 12)
             if (pl.k1b == 4) return pass_a_at<Real, LG, 4, 3>(pl, params, p0, np, inter, s);
+        // float-float: 512-thread CTAs of 2 columns (half the registers per thread of radix 16)
+        if constexpr (std::is_same<Real, ffloat>::value && LG >= 10 && LG <= 12)
+            if (pl.k1b == 2) return pass_a_at<Real, LG, 2, 3>(pl, params, p0, np, inter, s);
         return cudaErrorInvalidValue;
     }
     if (pl.k1b == KD) return pass_a_at<Real, LG, KD>(pl, params, p0, np, inter, s);

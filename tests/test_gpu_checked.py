@@ -74,6 +74,7 @@ def _cases(fc):
     cases.append(["64s", dict(base="C1"), "fp64", [None], 3])
     cases.append(["64s", dict(base="C1"), "ff", [None], 3])
     cases.append(["60min", dict(base="C2"), "fp32", [None], 2])
+    cases.append(["60min", dict(base="C2"), "ff", [None, [0, 2, 8, 4]], 1])   # radix-8 default, radix 16
     return cases
 
 

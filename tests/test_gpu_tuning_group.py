@@ -130,3 +130,22 @@ def test_group_of_mixed_precisions_equals_individual_searches():
                                                 box=box))
         assert got[s] == ref
         ctx.close()
+
+
+def test_float_float_radix8_shape_on_the_60min_transform():
+    """The float-float form's radix-8 pass A (512-thread CTAs of two 2048-point columns) against its
+    radix-16 pass A and the oracle."""
+    import paper_2002_02150_gb300 as fc
+    w = sd.C2
+    data = sd.make_dataset(w, 0)
+    theta = sd.make_particles(w, 4, seed=3)
+    with make_ctx(w, data, "ff", max_batch=4) as ctx:
+        info = fc.fcas_set_shape(ctx, 0, 2, 8, 4)
+        assert info["n2"] == 2048
+        ref_f, ref_t = gpu_fitness(ctx, theta)
+        info = fc.fcas_set_shape(ctx, 0, 2, 8, 3)
+        assert info["radix_bits_a"] == 3
+        f, t = gpu_fitness(ctx, theta)
+    np.testing.assert_allclose(f, ref_f, rtol=1e-12)
+    np.testing.assert_array_equal(t, ref_t)
+    assert_parity(oracle_setup(w, data), theta[:2], f[:2], t[:2], "ff", "radix-8 float-float")
