@@ -348,6 +348,17 @@ pass_b_kernel(const cplx<Real>* __restrict__ inter, const ParticleParams* __rest
     const int ta = blockIdx.x * TB + c;
     const int64_t p = blockIdx.y;
     if (!params[p0 + p].valid) return;   // the final reduce reports NaN for it
+    if constexpr (sizeof(Real) != 4) {
+        // binary64 and float-float: the second series' row is requested into L2 now, so that its
+        // loads after the first transform do not wait on DRAM (one 128-byte line per prefetch;
+        // float-float pass B 20.0 -> 17.8 ms per 64 particles of the 60-min workload, FP32 unchanged)
+        constexpr int LINE = 128 / (int)sizeof(C);
+        const C* row1 = inter + ((p * kSeries + 1) * n2 + ta) * (int64_t)L;
+        for (int e = j * LINE; e < L; e += G * LINE)
+            if (FCAS_CHECK(((p * kSeries + 1) * n2 + ta) * (int64_t)L + e < (int64_t)gridDim.y * kSeries * n2 * L,
+                           kCheckInterRead))
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(row1 + e));
+    }
 
     Real g[V];
 #pragma unroll
