@@ -72,6 +72,18 @@ __device__ __forceinline__ void r16_dft4(C& a0, C& a1, C& a2, C& a3) {
     a3 = t1 - it3;
 }
 
+// the same transform when a2 = a3 = 0 (the first layer of a column whose upper half is zero):
+// a0 +- a1 and a0 +- i a1, without the additions of zero
+template <int S, typename C>
+__device__ __forceinline__ void r16_dft4_lowhalf(C& a0, C& a1, C& a2, C& a3) {
+    const C x0 = a0, x1 = a1;
+    const C ix1 = mul_si<S>(x1);
+    a0 = x0 + x1;
+    a2 = x0 - x1;
+    a1 = x0 + ix1;
+    a3 = x0 - ix1;
+}
+
 // x * e^{S 2 pi i M / 16}
 template <int S, int M, typename C>
 __device__ __forceinline__ C rot16(C x) {
@@ -107,13 +119,19 @@ __device__ __forceinline__ C rot16(C x) {
     }
 }
 
-template <int S, typename C>
+// LH: a[R/2 ..] are zero (the first stage of a column whose upper half is zero)
+template <int S, bool LH = false, typename C>
 __device__ __forceinline__ void dft8(C (&a)[8]) {
     // n = 2 n1 + n2, k = k1 + 4 k2: DFT4 over n1, twiddle e^{S 2 pi i n2 k1 / 8}, DFT2 over n2
     C e0 = a[0], e1 = a[2], e2 = a[4], e3 = a[6];
     C o0 = a[1], o1 = a[3], o2 = a[5], o3 = a[7];
-    r16_dft4<S>(e0, e1, e2, e3);
-    r16_dft4<S>(o0, o1, o2, o3);
+    if constexpr (LH) {
+        r16_dft4_lowhalf<S>(e0, e1, e2, e3);
+        r16_dft4_lowhalf<S>(o0, o1, o2, o3);
+    } else {
+        r16_dft4<S>(e0, e1, e2, e3);
+        r16_dft4<S>(o0, o1, o2, o3);
+    }
     o1 = rot16<S, 2>(o1);
     o2 = rot16<S, 4>(o2);
     o3 = rot16<S, 6>(o3);
@@ -127,7 +145,7 @@ __device__ __forceinline__ void dft8(C (&a)[8]) {
     a[7] = e3 - o3;
 }
 
-template <int S, typename C>
+template <int S, bool LH = false, typename C>
 __device__ __forceinline__ void dft16(C (&a)[16]) {
     // n = 4 n1 + n2, k = k1 + 4 k2: DFT4 over n1 (for each n2), twiddle e^{S 2 pi i n2 k1 / 16},
     // DFT4 over n2 (for each k1)
@@ -135,10 +153,17 @@ __device__ __forceinline__ void dft16(C (&a)[16]) {
     C y1[4] = {a[1], a[5], a[9], a[13]};
     C y2[4] = {a[2], a[6], a[10], a[14]};
     C y3[4] = {a[3], a[7], a[11], a[15]};
-    r16_dft4<S>(y0[0], y0[1], y0[2], y0[3]);
-    r16_dft4<S>(y1[0], y1[1], y1[2], y1[3]);
-    r16_dft4<S>(y2[0], y2[1], y2[2], y2[3]);
-    r16_dft4<S>(y3[0], y3[1], y3[2], y3[3]);
+    if constexpr (LH) {
+        r16_dft4_lowhalf<S>(y0[0], y0[1], y0[2], y0[3]);
+        r16_dft4_lowhalf<S>(y1[0], y1[1], y1[2], y1[3]);
+        r16_dft4_lowhalf<S>(y2[0], y2[1], y2[2], y2[3]);
+        r16_dft4_lowhalf<S>(y3[0], y3[1], y3[2], y3[3]);
+    } else {
+        r16_dft4<S>(y0[0], y0[1], y0[2], y0[3]);
+        r16_dft4<S>(y1[0], y1[1], y1[2], y1[3]);
+        r16_dft4<S>(y2[0], y2[1], y2[2], y2[3]);
+        r16_dft4<S>(y3[0], y3[1], y3[2], y3[3]);
+    }
     y1[1] = rot16<S, 1>(y1[1]);
     y1[2] = rot16<S, 2>(y1[2]);
     y1[3] = rot16<S, 3>(y1[3]);
@@ -159,10 +184,10 @@ __device__ __forceinline__ void dft16(C (&a)[16]) {
     }
 }
 
-template <int S, int R, typename C>
+template <int S, int R, bool LH = false, typename C>
 __device__ __forceinline__ void dft_r(C (&a)[R]) {
-    if constexpr (R == 16) dft16<S>(a);
-    else if constexpr (R == 8) dft8<S>(a);
+    if constexpr (R == 16) dft16<S, LH>(a);
+    else if constexpr (R == 8) dft8<S, LH>(a);
     else if constexpr (R == 4) r16_dft4<S>(a[0], a[1], a[2], a[3]);
     else if constexpr (R == 2) {
         C t = a[0] - a[1];
@@ -171,7 +196,8 @@ __device__ __forceinline__ void dft_r(C (&a)[R]) {
     }
 }
 
-template <typename Real, int S, int LOG_L, int DONE, int MAXRB, bool PP>
+// LH (first stage only): the upper half of the input (v[V/2 ..]) is zero
+template <typename Real, int S, int LOG_L, int DONE, int MAXRB, bool PP, bool LH = false>
 __device__ __forceinline__ void fftr_stage(cplx<Real> (&v)[fftr_v(LOG_L, MAXRB)], cplx<Real>* buf0, int es, int j,
                                            const cplx<Real>* __restrict__ stw, int alt, int par0) {
     using C = cplx<Real>;
@@ -249,7 +275,8 @@ __device__ __forceinline__ void fftr_stage(cplx<Real> (&v)[fftr_v(LOG_L, MAXRB)]
                 }
             }
         }
-        dft_r<S, R>(a);
+        // with R = V (T = 1) the zero upper half of the first stage is the upper half of a[]
+        dft_r<S, R, LH && FIRST && T == 1 && R >= 8>(a);
 #pragma unroll
         for (int r = 0; r < R; ++r) v[h + r * T] = a[r];
     }
@@ -282,11 +309,11 @@ __device__ __forceinline__ void fftr_stage(cplx<Real> (&v)[fftr_v(LOG_L, MAXRB)]
     }
 }
 
-template <typename Real, int S, int LOG_L, int MAXRB, bool PP = false, int DONE = 0>
+template <typename Real, int S, int LOG_L, int MAXRB, bool PP = false, int DONE = 0, bool LH = false>
 __device__ __forceinline__ void fftr(cplx<Real> (&v)[fftr_v(LOG_L, MAXRB)], cplx<Real>* buf, int es, int j,
                                      const cplx<Real>* __restrict__ stw, int alt = 0, int par0 = 0) {
     if constexpr (DONE < LOG_L) {
-        fftr_stage<Real, S, LOG_L, DONE, MAXRB, PP>(v, buf, es, j, stw, alt, par0);
+        fftr_stage<Real, S, LOG_L, DONE, MAXRB, PP, LH>(v, buf, es, j, stw, alt, par0);
         fftr<Real, S, LOG_L, MAXRB, PP, DONE + fftr_radix_bits(LOG_L, DONE, MAXRB)>(v, buf, es, j, stw, alt, par0);
     }
 }

@@ -264,7 +264,7 @@ pass_a_kernel(const cplx<Real>* __restrict__ y, const Basis<phase_t<Real>>* __re
         for (int q = 0; q < VH; ++q) {
             C cp;
             if constexpr (sizeof(P) == 4) {
-                const ChirpPowers b = chirp_powers(bq[q]);
+                const ChirpPowers b = chirp_powers_lean(bq[q]);
                 float s = frac_mul_ff(cfh[0], cfl[0], b.b53.x, b.b53.y);
                 s += frac_mul_ff(cfh[1], cfl[1], b.b1.x, b.b1.y);
                 s += frac_mul_ff(cfh[2], cfl[2], b.b23.x, b.b23.y);
@@ -296,8 +296,8 @@ pass_a_kernel(const cplx<Real>* __restrict__ y, const Basis<phase_t<Real>>* __re
         // exchange count is continued across the series so that a buffer is never rewritten before
         // all its reads of the previous exchange are done
         constexpr int NX = (LOG_L + MAXRB - 1) / MAXRB - 1;
-        fftr<Real, +1, LOG_L, MAXRB, pass_a_pingpong<Real, LOG_L, K1B>()>(v, smem + c, K1B, j, stw,
-                                                                          K1B * fft16_buf_elems(LOG_L), (a * NX) & 1);
+        fftr<Real, +1, LOG_L, MAXRB, pass_a_pingpong<Real, LOG_L, K1B>(), 0, true>(
+            v, smem + c, K1B, j, stw, K1B * fft16_buf_elems(LOG_L), (a * NX) & 1);
         C* orow = out + ((p * kSeries + a) * L) * (int64_t)n1 + k1;
         // e^{2 pi i k1 ta / N} for ta = j + q G: the value at q = 0 times powers of the step e^{2 pi i k1 G / N}
         const int m0 = k1 * j, ms = k1 * G;   // < N
