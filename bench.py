@@ -744,9 +744,13 @@ def oracle_pool(w, seed, theta, steps):
 
 def cpu_baseline(w, seed, theta, steps):
     n, step_s = oracle_pool(w, seed, theta, steps)
-    return {"value": round(n * steps / sum(step_s), 4), "unit": UNIT, "cores": n, "kind": "oracle",
+    value = n * steps / sum(step_s)
+    return {"value": round(value, 4), "unit": UNIT, "cores": n, "kind": "oracle",
             "sample": f"{n * steps} particles of the same workload ({steps} per core), FP64 numpy oracle, "
-                      f"{n} single-threaded processes, data preparation excluded"}
+                      f"{n} single-threaded processes, data preparation excluded",
+            "s_per_eval_per_core": round(n / value, 3),
+            "search_s_extrapolated": {"value": round(PSO_EVALS / value, 1),
+                                      "how": "8 runs x 40 particles x 2000 iterations / value (extrapolated, not run)"}}
 
 
 def bench_reference(args, ranks):
