@@ -65,7 +65,8 @@ def test_noiseless_injection_gives_snr_squared(precision):
 
 
 @pytest.mark.parametrize("precision", FORMS)
-@pytest.mark.parametrize("dets", [("L1",), ("H1", "V1"), ("H1", "L1", "V1"), ("H1", "L1", "V1", "K1", "H1")])
+@pytest.mark.parametrize("dets", [("L1",), ("H1", "V1"), ("H1", "L1", "V1"), ("H1", "L1", "V1", "K1", "H1"),
+                                  ("H1", "L1", "V1", "K1", "H1", "L1", "V1", "K1")])   # up to FCAS_MAX_DET
 def test_network_sizes(precision, dets):
     w = dataclasses.replace(sd.SMALL, detectors=dets)
     data = sd.make_dataset(w, 5)
@@ -176,15 +177,18 @@ def test_config2_full_size_sampled():
 
 def test_largest_supported_length_sampled():
     """N = 2^24 (the largest transform the two passes cover: 2^12 x 2^12), a ragged data length
-    and a two-detector network; the first particles match the oracle one by one in the FP32 form."""
+    and a two-detector network; the first particles match the oracle one by one in the FP32 and
+    float-float forms."""
     w = dataclasses.replace(sd.C2, detectors=("H1", "L1"), n_fft=1 << 24, n_samples=(1 << 24) - 12345, fs=4096.0,
                             f_low=30.0, f_high=1500.0, arrival_s=2000.0, n_particles=6)
     data = sd.make_dataset(w, 7)
     theta = sd.make_particles(w, seed=7)
-    with make_ctx(w, data, "fp32") as ctx:
-        fit, tc = gpu_fitness(ctx, theta)
-    assert np.all(np.isfinite(fit)) and np.all((tc >= 0) & (tc < w.n_samples))
-    assert_parity(oracle_setup(w, data), theta[:2], fit[:2], tc[:2], "fp32", "N=2^24")
+    setup = oracle_setup(w, data)
+    for precision in ("fp32", "ff"):
+        with make_ctx(w, data, precision) as ctx:
+            fit, tc = gpu_fitness(ctx, theta)
+        assert np.all(np.isfinite(fit)) and np.all((tc >= 0) & (tc < w.n_samples))
+        assert_parity(setup, theta[:2], fit[:2], tc[:2], precision, f"N=2^24 {precision}")
 
 
 def test_two_contexts_on_two_streams_match_sequential_results():
