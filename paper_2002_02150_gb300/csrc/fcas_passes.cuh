@@ -67,10 +67,10 @@ __device__ __forceinline__ double2 unit_phasor(double turns) {
 constexpr int kPhaseTabBits = 10;
 constexpr int kPhaseTab = 1 << kPhaseTabBits;
 
-// e^{2 pi i u} in float-float for |u| <= 1/2 given in binary64, on the FP32 units (table-driven
-// reduction in the manner of Tang 1990): u = m / 1024 + r with the nearest table point m, and
-// e^{2 pi i u} = T[m] (cos x + i sin x), x = 2 pi r, |x| <= pi / 1024. The remainder is exact in
-// float-float (u split into two floats, the table point subtracted exactly by a fused multiply-add);
+// e^{2 pi i u} in float-float for a float-float |u| <= 1/2 (or a binary64 u, split into two floats),
+// on the FP32 units (table-driven reduction in the manner of Tang 1990): u = m / 1024 + r with the
+// nearest table point m, and e^{2 pi i u} = T[m] (cos x + i sin x), x = 2 pi r, |x| <= pi / 1024. The
+// remainder is exact in float-float (the table point subtracted exactly by a fused multiply-add);
 // sin x = x - x^3/6 + x^5/120 and cos x = 1 - x^2/2 + x^4/24 (Taylor; the first omitted terms are
 // below 2e-18), with x and x^2 in float-float and the small terms in float. Absolute error a few
 // units of 2^-48.
@@ -128,8 +128,9 @@ __host__ __device__ constexpr bool pass_a_pingpong() {
     return 2 * sizeof(cplx<Real>) * (size_t)K1B * fft16_buf_elems(LOG_L) <= 200 * 1024;
 }
 
-// The float-float form reduces the chirp and delay phases in binary64 (basis and delays as in the
-// binary64 form) and forms the phasors, the detector sums and everything after them in float-float.
+// The float-float form reduces the chirp phase in binary64 (basis as in the binary64 form) and the
+// delay phase from a three-float split of the delay, and forms the phasors, the detector sums and
+// everything after them in float-float.
 template <typename Real> struct phase_of { using type = Real; };
 template <> struct phase_of<ffloat> { using type = double; };
 template <typename Real> using phase_t = typename phase_of<Real>::type;
