@@ -196,8 +196,10 @@ __device__ __forceinline__ void dft_r(C (&a)[R]) {
     }
 }
 
-// LH (first stage only): the upper half of the input (v[V/2 ..]) is zero
-template <typename Real, int S, int LOG_L, int DONE, int MAXRB, bool PP, bool LH = false>
+// LH (first stage only): the upper half of the input (v[V/2 ..]) is zero. TWL: the stage twiddles
+// w^r (r < 4) and w^{4h} come from the table and the rest as one product each (instead of w and w^4
+// loaded and the other powers formed by products); fewer instructions, a few more registers.
+template <typename Real, int S, int LOG_L, int DONE, int MAXRB, bool PP, bool LH = false, bool TWL = false>
 __device__ __forceinline__ void fftr_stage(cplx<Real> (&v)[fftr_v(LOG_L, MAXRB)], cplx<Real>* buf0, int es, int j,
                                            const cplx<Real>* __restrict__ stw, int alt, int par0) {
     using C = cplx<Real>;
@@ -238,7 +240,31 @@ __device__ __forceinline__ void fftr_stage(cplx<Real> (&v)[fftr_v(LOG_L, MAXRB)]
         if constexpr (NS > 1) {
             const int jm = jj & (NS - 1);
             const C* t = stw + (NS - 1) + jm;
-            if constexpr (R >= 8 && !std::is_same<Real, ffloat>::value) {
+            if constexpr (R >= 8 && TWL && !std::is_same<Real, ffloat>::value) {
+                C wl[4], wh[R / 4];
+                wl[0] = wh[0] = mkc((Real)1, (Real)0);
+#pragma unroll
+                for (int r = 1; r < 4; ++r) {
+                    wl[r] = wl[0];
+                    if (FCAS_CHECK((NS - 1) + jm + (r - 1) * NS < L, kCheckTwiddle)) wl[r] = ldg_c(t + (r - 1) * NS);
+                    if constexpr (S < 0) wl[r] = cconj(wl[r]);
+                }
+#pragma unroll
+                for (int hi = 1; hi < R / 4; ++hi) {
+                    wh[hi] = wh[0];
+                    if (FCAS_CHECK((NS - 1) + jm + (4 * hi - 1) * NS < L, kCheckTwiddle))
+                        wh[hi] = ldg_c(t + (4 * hi - 1) * NS);
+                    if constexpr (S < 0) wh[hi] = cconj(wh[hi]);
+                }
+#pragma unroll
+                for (int r = 1; r < 4; ++r) a[r] = cmul(a[r], wl[r]);
+#pragma unroll
+                for (int hi = 1; hi < R / 4; ++hi) {
+                    a[4 * hi] = cmul(a[4 * hi], wh[hi]);
+#pragma unroll
+                    for (int r = 1; r < 4; ++r) a[4 * hi + r] = cmul(a[4 * hi + r], cmul(wh[hi], wl[r]));
+                }
+            } else if constexpr (R >= 8 && !std::is_same<Real, ffloat>::value) {
                 // w^r for r = 1..R-1 from two table entries: w and w^4 (powers by products, <= 3 roundings);
                 // the float-float form loads every power instead (a double-word product costs more
                 // than a load)
@@ -309,12 +335,13 @@ __device__ __forceinline__ void fftr_stage(cplx<Real> (&v)[fftr_v(LOG_L, MAXRB)]
     }
 }
 
-template <typename Real, int S, int LOG_L, int MAXRB, bool PP = false, int DONE = 0, bool LH = false>
+template <typename Real, int S, int LOG_L, int MAXRB, bool PP = false, int DONE = 0, bool LH = false, bool TWL = false>
 __device__ __forceinline__ void fftr(cplx<Real> (&v)[fftr_v(LOG_L, MAXRB)], cplx<Real>* buf, int es, int j,
                                      const cplx<Real>* __restrict__ stw, int alt = 0, int par0 = 0) {
     if constexpr (DONE < LOG_L) {
-        fftr_stage<Real, S, LOG_L, DONE, MAXRB, PP, LH>(v, buf, es, j, stw, alt, par0);
-        fftr<Real, S, LOG_L, MAXRB, PP, DONE + fftr_radix_bits(LOG_L, DONE, MAXRB)>(v, buf, es, j, stw, alt, par0);
+        fftr_stage<Real, S, LOG_L, DONE, MAXRB, PP, LH, TWL>(v, buf, es, j, stw, alt, par0);
+        fftr<Real, S, LOG_L, MAXRB, PP, DONE + fftr_radix_bits(LOG_L, DONE, MAXRB), false, TWL>(v, buf, es, j, stw, alt,
+                                                                                              par0);
     }
 }
 
