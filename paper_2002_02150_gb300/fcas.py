@@ -299,12 +299,23 @@ def pso_config(n_runs=8, n_particles=40, n_iter=2000, n_neighbours=1, seed=0, bo
     return cfg
 
 
+def _check_swarm(cfg, x=(), flat=()):
+    """The device kernels address n_runs x n_particles rows: every (rows, 4) float64 array in x and
+    every (rows,) array in flat must be a contiguous CUDA tensor of exactly that size."""
+    rows = int(cfg.n_runs) * int(cfg.n_particles)
+    for t, shape in [(t, (rows, 4)) for t in x] + [(t, (rows,)) for t in flat]:
+        if not (_is_torch(t) and t.is_cuda and t.is_contiguous() and tuple(t.shape) == shape and t.element_size() == 8):
+            raise FcasError(-1, f"swarm arrays must be contiguous 8-byte CUDA tensors of shape {shape} "
+                                f"(n_runs x n_particles = {rows} rows)")
+
+
 def pso_theta(cfg, x, theta=None, stream=None):
     """Parameters of normalised positions x (torch CUDA (rows, 4)) by the library's kernel; NaN outside
     the box (not evaluated)."""
     import torch
     if theta is None:
         theta = torch.empty_like(x)
+    _check_swarm(cfg, x=(x, theta))
     _check(load_library().fcas_pso_theta(ctypes.byref(cfg), ctypes.c_void_p(x.data_ptr()),
                                          ctypes.c_void_p(theta.data_ptr()), _stream(stream, x)))
     return theta
@@ -316,14 +327,76 @@ def _state(x, v, pbest_x, pbest_f, pbest_tc):
 
 def fcas_pso_init(cfg, x, v, pbest_x, pbest_f, pbest_tc, stream=None):
     """Initialise device state tensors (torch CUDA, float64 / int64, rows = n_runs * n_particles)."""
+    _check_swarm(cfg, x=(x, v, pbest_x), flat=(pbest_f, pbest_tc))
     st = _state(x, v, pbest_x, pbest_f, pbest_tc)
     _check(load_library().fcas_pso_init(ctypes.byref(cfg), ctypes.byref(st), _stream(stream, x)))
 
 
 def fcas_pso_update(cfg, it, fitness, tc, x, v, pbest_x, pbest_f, pbest_tc, stream=None):
+    _check_swarm(cfg, x=(x, v, pbest_x), flat=(pbest_f, pbest_tc, fitness, tc))
     st = _state(x, v, pbest_x, pbest_f, pbest_tc)
     _check(load_library().fcas_pso_update(ctypes.byref(cfg), int(it), ctypes.c_void_p(fitness.data_ptr()),
                                           ctypes.c_void_p(tc.data_ptr()), ctypes.byref(st), _stream(stream, x)))
+
+
+def pso_save(path, cfg, it, x, v, pbest_x, pbest_f, pbest_tc):
+    """Checkpoint: the swarm state after iteration `it` (tensors or arrays) and its configuration, as
+    an .npz file written atomically (a temporary file, then a rename)."""
+    arrays = {k: (t.detach().cpu().numpy() if _is_torch(t) else np.asarray(t))
+              for k, t in zip(("x", "v", "pbest_x", "pbest_f", "pbest_tc"), (x, v, pbest_x, pbest_f, pbest_tc))}
+    tmp = path + ".tmp.npz"
+    np.savez(tmp, it=np.int64(it), cfg=np.frombuffer(bytes(cfg), dtype=np.uint8), **arrays)
+    os.replace(tmp, path)
+
+
+def pso_load(path, device=None):
+    """Read a checkpoint: (cfg, it, [x, v, pbest_x, pbest_f, pbest_tc]); the state as torch tensors on
+    `device`, or numpy arrays when device is None."""
+    with np.load(path) as z:
+        cfg = fcas_pso_config.from_buffer_copy(z["cfg"].tobytes())
+        it = int(z["it"])
+        state = [z[k].copy() for k in ("x", "v", "pbest_x", "pbest_f", "pbest_tc")]
+    if device is not None:
+        import torch
+        state = [torch.from_numpy(a).to(device) for a in state]
+    return cfg, it, state
+
+
+def pso_run(ctx, cfg, checkpoint=None, every=0, resume=False, stop_after=None, device="cuda:0"):
+    """The PSO search iteration by iteration through fcas_pso_theta / fcas_fitness / fcas_pso_update
+    (the same steps as fcas_search, without its graph replay), checkpointing the swarm to
+    `checkpoint` every `every` iterations and, with resume=True, continuing from the checkpoint when
+    one exists (its configuration must equal cfg). The counter-based random numbers make a resumed
+    run identical to an uninterrupted one. stop_after ends the run after that many iterations of this
+    call (an interruption). Returns (results per run as fcas_search reports them, iterations done)."""
+    import torch
+    rows = cfg.n_runs * cfg.n_particles
+    start = 0
+    if resume and checkpoint and os.path.exists(checkpoint):
+        saved_cfg, it, state = pso_load(checkpoint, device)
+        if bytes(saved_cfg) != bytes(cfg):
+            raise FcasError(-1, "pso_run: the checkpoint was written for another configuration")
+        start = it + 1
+    else:
+        x = torch.empty((rows, 4), dtype=torch.float64, device=device)
+        state = [x, torch.empty_like(x), torch.empty_like(x), torch.empty(rows, dtype=torch.float64, device=device),
+                 torch.empty(rows, dtype=torch.int64, device=device)]
+        fcas_pso_init(cfg, *state)
+    stop = cfg.n_iter if stop_after is None else min(cfg.n_iter, start + int(stop_after))
+    it = start - 1
+    for it in range(start, stop):
+        theta = pso_theta(cfg, state[0])
+        fit, tc = fcas_fitness(ctx, theta)
+        fcas_pso_update(cfg, it, fit, tc, *state)
+        if checkpoint and every and ((it + 1) % every == 0 or it + 1 == cfg.n_iter):
+            pso_save(checkpoint, cfg, it, *state)
+    pbest_f = state[3].view(cfg.n_runs, cfg.n_particles)
+    best = torch.argmax(torch.nan_to_num(pbest_f, nan=-np.inf), dim=1)   # first maximum of each run
+    idx = torch.arange(cfg.n_runs, device=pbest_f.device) * cfg.n_particles + best
+    theta = pso_theta(cfg, state[2])[idx].cpu().numpy()   # the kernel maps all n_runs x n_particles rows
+    f, t = state[3][idx].cpu().numpy(), state[4][idx].cpu().numpy()
+    res = [dict(fitness=float(f[r]), theta=list(theta[r]), tc=int(t[r])) for r in range(cfg.n_runs)]
+    return res, it + 1
 
 
 def fcas_search(ctx, cfg, stream=None):

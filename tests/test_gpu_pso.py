@@ -161,3 +161,27 @@ def test_checkpoint_and_resume_is_bit_identical():
         torch.cuda.synchronize()
     for u, v in zip(a, c):
         assert torch.equal(u, v)
+
+
+def test_pso_run_resumes_from_a_checkpoint_file(tmp_path):
+    """pso_run interrupted after 5 of 8 iterations and resumed from its last checkpoint file (written
+    after iteration 4) ends exactly where an uninterrupted run ends, which is also what fcas_search
+    (the same steps replayed as a graph) reports."""
+    import paper_2002_02150_gb300 as fc
+    w = sd.SMALL
+    data = sd.make_dataset(w, 4)
+    _, cfg = _cfgs(w, n_runs=2, n_particles=10, n_iter=8, seed=23)
+    path = str(tmp_path / "swarm.npz")
+    with make_ctx(w, data, "fp32") as ctx:
+        full, n_full = fc.pso_run(ctx, cfg)
+        part, n_part = fc.pso_run(ctx, cfg, checkpoint=path, every=2, stop_after=5)
+        _, it, _ = fc.pso_load(path)
+        resumed, n_res = fc.pso_run(ctx, cfg, checkpoint=path, every=2, resume=True)
+        searched = fc.fcas_search(ctx, cfg)
+        _, other = _cfgs(w, n_runs=2, n_particles=10, n_iter=8, seed=24)
+        with pytest.raises(fc.FcasError):
+            fc.pso_run(ctx, other, checkpoint=path, resume=True)
+    assert (n_full, n_part, it, n_res) == (8, 5, 3, 8)
+    for a, b, s in zip(full, resumed, searched):
+        assert a == b
+        assert a["fitness"] == s["fitness"] and a["tc"] == s["tc"] and a["theta"] == s["theta"]
