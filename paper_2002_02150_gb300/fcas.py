@@ -461,14 +461,14 @@ def coherent_fitness(ctx, theta):
     return _CF.apply(theta, ctx)
 
 
-def polish(ctx, theta, steps=10, scales=(1e-2, 1e-2, 1e-4, 1e-4), judge=None, max_halvings=30):
+def polish(ctx, theta, steps=10, scales=(1e-2, 1e-2, 1e-4, 1e-4), evaluate=None, max_halvings=30):
     """Gradient ascent from theta (n, 4) numpy: each step moves by s^2 g / |s g| (s = scales, relative
-    for the chirp times) and halves the step until the judge's fitness increases (default judge: this
+    for the chirp times) and halves the step until the fitness given by `evaluate` increases (default: this
     library's fitness). Returns (theta, fitness, accepted steps) per particle."""
     theta = np.array(theta, dtype=np.float64)
-    if judge is None:
-        judge = lambda th: fcas_fitness(ctx, th)
-    fit, tc = judge(theta)
+    if evaluate is None:
+        evaluate = lambda th: fcas_fitness(ctx, th)
+    fit, tc = evaluate(theta)
     fit = np.array(fit, dtype=np.float64)
     tc = np.array(tc, dtype=np.int64)
     accepted = np.zeros(len(theta), dtype=np.int64)
@@ -482,7 +482,7 @@ def polish(ctx, theta, steps=10, scales=(1e-2, 1e-2, 1e-4, 1e-4), judge=None, ma
             if np.all(done):
                 break
             cand = theta + step[:, None] * direction
-            f2, t2 = judge(cand)
+            f2, t2 = evaluate(cand)
             f2 = np.array(f2)
             ok = (~done) & (f2 > fit)
             theta[ok] = cand[ok]

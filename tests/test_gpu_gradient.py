@@ -95,9 +95,9 @@ def test_autograd_function_uses_the_adjoint():
     torch.testing.assert_close(theta.grad, 2.0 * g)
 
 
-def test_polish_improves_pso_best_particles_judged_by_the_oracle():
+def test_polish_improves_pso_best_particles_measured_by_the_oracle():
     """10 gradient-polish steps on each run's best particle; steps are accepted only when the FP64
-    oracle's fitness increases, so the oracle-judged gain is >= 0 and positive on some runs."""
+    oracle's fitness increases, so the gain the oracle measures is >= 0 and positive on some runs."""
     import paper_2002_02150_gb300 as fc
     w = sd.C1
     data = sd.make_dataset(w, 0)
@@ -109,8 +109,8 @@ def test_polish_improves_pso_best_particles_judged_by_the_oracle():
         res = fc.fcas_search(ctx, cfg)
         theta = np.array([r["theta"] for r in res])
         before = np.array([o.fitness(setup, th)[0] for th in theta])
-        judge = lambda th: tuple(np.array(v) for v in zip(*[o.fitness(setup, t) for t in th]))
-        th2, after, acc = fc.polish(ctx, theta, steps=10, judge=judge)
+        by_oracle = lambda th: tuple(np.array(v) for v in zip(*[o.fitness(setup, t) for t in th]))
+        th2, after, acc = fc.polish(ctx, theta, steps=10, evaluate=by_oracle)
     assert np.all(after >= before)
     assert np.any(after > before)
 
