@@ -45,6 +45,10 @@ __host__ __device__ constexpr int fft16_radix_bits(int log_l, int done) { return
 __host__ __device__ constexpr int fft16_v(int log_l) { return fftr_v(log_l, 4); }
 __host__ __device__ constexpr int fft16_pad(int e) { return e + (e >> 4); }
 __host__ __device__ constexpr int fft16_buf_elems(int log_l) { return fft16_pad(1 << log_l); }
+// the exchange padding with one spare element per 2^PS (PS = 4 above; 3 for 16-byte elements in
+// radix-8 stages, whose first-stage writes would otherwise fall two to a bank group)
+template <int PS> __host__ __device__ constexpr int xpad(int e) { return e + (e >> PS); }
+template <int PS> __host__ __device__ constexpr int xbuf_elems(int log_l) { return xpad<PS>(1 << log_l); }
 
 // Checked build (FCAS_CHECKED): the fitness kernels recompute each shared-memory, table and global
 // index from its definition and range-test it; a failed test sets bit `bit` of this flag (read and
@@ -199,7 +203,7 @@ __device__ __forceinline__ void dft_r(C (&a)[R]) {
 // LH (first stage only): the upper half of the input (v[V/2 ..]) is zero. TWL: the stage twiddles
 // w^r (r < 4) and w^{4h} come from the table and the rest as one product each (instead of w and w^4
 // loaded and the other powers formed by products); fewer instructions, a few more registers.
-template <typename Real, int S, int LOG_L, int DONE, int MAXRB, bool PP, bool LH = false, bool TWL = false>
+template <typename Real, int S, int LOG_L, int DONE, int MAXRB, bool PP, bool LH = false, bool TWL = false, int PS = 4>
 __device__ __forceinline__ void fftr_stage(cplx<Real> (&v)[fftr_v(LOG_L, MAXRB)], cplx<Real>* buf0, int es, int j,
                                            const cplx<Real>* __restrict__ stw, int alt, int par0) {
     using C = cplx<Real>;
@@ -215,20 +219,20 @@ __device__ __forceinline__ void fftr_stage(cplx<Real> (&v)[fftr_v(LOG_L, MAXRB)]
     constexpr int ST = DONE / MAXRB;
     if constexpr (!FIRST) {
         const cplx<Real>* buf = (PP && ((ST - 1 + par0) & 1)) ? buf0 + alt : buf0;
-        if constexpr (G % 16 == 0) {
-            // pad(j + q G) = pad(j) + q (G + G/16): one base address, constant offsets
-            const C* rb = buf + fft16_pad(j) * es;
+        if constexpr (G % (1 << PS) == 0) {
+            // pad(j + q G) = pad(j) + q (G + G / 2^PS): one base address, constant offsets
+            const C* rb = buf + xpad<PS>(j) * es;
 #pragma unroll
             for (int q = 0; q < V; ++q) {
-                const int e = fft16_pad(j) + q * (G + G / 16);
-                if (FCAS_CHECK(e == fft16_pad(j + q * G) && e < fft16_buf_elems(LOG_L), kCheckExchangeRead))
-                    v[q] = rb[q * (G + G / 16) * es];
+                const int e = xpad<PS>(j) + q * (G + (G >> PS));
+                if (FCAS_CHECK(e == xpad<PS>(j + q * G) && e < xbuf_elems<PS>(LOG_L), kCheckExchangeRead))
+                    v[q] = rb[q * (G + (G >> PS)) * es];
             }
         } else {
 #pragma unroll
             for (int q = 0; q < V; ++q)
-                if (FCAS_CHECK(fft16_pad(j + q * G) < fft16_buf_elems(LOG_L), kCheckExchangeRead))
-                    v[q] = buf[fft16_pad(j + q * G) * es];
+                if (FCAS_CHECK(xpad<PS>(j + q * G) < xbuf_elems<PS>(LOG_L), kCheckExchangeRead))
+                    v[q] = buf[xpad<PS>(j + q * G) * es];
         }
     }
 #pragma unroll
@@ -313,35 +317,38 @@ __device__ __forceinline__ void fftr_stage(cplx<Real> (&v)[fftr_v(LOG_L, MAXRB)]
         for (int h = 0; h < T; ++h) {
             const int jj = j + h * G;
             const int dst = (jj / NS) * NS * R + (jj & (NS - 1));
-            // pad(dst + r NS) = pad(dst) + r NS + (r NS >> 4) when adding r NS to dst never carries into
-            // a new group of 16 differently from r NS itself: NS a multiple of 16, or NS dividing 16
-            // with NS R a multiple of 16 (dst mod 16 < NS), or NS = 1 with R = 8 (dst mod 16 in {0, 8})
-            if constexpr (NS % 16 == 0 || (16 % NS == 0 && (NS * R) % 16 == 0) || (NS == 1 && R == 8)) {
-                C* wb = buf + fft16_pad(dst) * es;
+            // pad(dst + r NS) = pad(dst) + r NS + (r NS >> PS) when adding r NS to dst never carries
+            // into a new group of 2^PS differently from r NS itself: NS a multiple of 2^PS, or NS
+            // dividing 2^PS with NS R a multiple of 2^PS (dst mod 2^PS < NS), or PS = 4, NS = 1 and
+            // R = 8 (dst mod 16 in {0, 8})
+            constexpr int GP = 1 << PS;
+            if constexpr (NS % GP == 0 || (GP % NS == 0 && (NS * R) % GP == 0) || (PS == 4 && NS == 1 && R == 8)) {
+                C* wb = buf + xpad<PS>(dst) * es;
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    const int e = fft16_pad(dst) + r * NS + ((r * NS) >> 4);
-                    if (FCAS_CHECK(e == fft16_pad(dst + r * NS) && e < fft16_buf_elems(LOG_L), kCheckExchangeWrite))
-                        wb[(r * NS + ((r * NS) >> 4)) * es] = v[h + r * T];
+                    const int e = xpad<PS>(dst) + r * NS + ((r * NS) >> PS);
+                    if (FCAS_CHECK(e == xpad<PS>(dst + r * NS) && e < xbuf_elems<PS>(LOG_L), kCheckExchangeWrite))
+                        wb[(r * NS + ((r * NS) >> PS)) * es] = v[h + r * T];
                 }
             } else {
 #pragma unroll
                 for (int r = 0; r < R; ++r)
-                    if (FCAS_CHECK(fft16_pad(dst + r * NS) < fft16_buf_elems(LOG_L), kCheckExchangeWrite))
-                        buf[fft16_pad(dst + r * NS) * es] = v[h + r * T];
+                    if (FCAS_CHECK(xpad<PS>(dst + r * NS) < xbuf_elems<PS>(LOG_L), kCheckExchangeWrite))
+                        buf[xpad<PS>(dst + r * NS) * es] = v[h + r * T];
             }
         }
         __syncthreads();
     }
 }
 
-template <typename Real, int S, int LOG_L, int MAXRB, bool PP = false, int DONE = 0, bool LH = false, bool TWL = false>
+template <typename Real, int S, int LOG_L, int MAXRB, bool PP = false, int DONE = 0, bool LH = false, bool TWL = false,
+          int PS = 4>
 __device__ __forceinline__ void fftr(cplx<Real> (&v)[fftr_v(LOG_L, MAXRB)], cplx<Real>* buf, int es, int j,
                                      const cplx<Real>* __restrict__ stw, int alt = 0, int par0 = 0) {
     if constexpr (DONE < LOG_L) {
-        fftr_stage<Real, S, LOG_L, DONE, MAXRB, PP, LH, TWL>(v, buf, es, j, stw, alt, par0);
-        fftr<Real, S, LOG_L, MAXRB, PP, DONE + fftr_radix_bits(LOG_L, DONE, MAXRB), false, TWL>(v, buf, es, j, stw, alt,
-                                                                                              par0);
+        fftr_stage<Real, S, LOG_L, DONE, MAXRB, PP, LH, TWL, PS>(v, buf, es, j, stw, alt, par0);
+        fftr<Real, S, LOG_L, MAXRB, PP, DONE + fftr_radix_bits(LOG_L, DONE, MAXRB), false, TWL, PS>(v, buf, es, j, stw,
+                                                                                                  alt, par0);
     }
 }
 

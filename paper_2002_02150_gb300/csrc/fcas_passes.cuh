@@ -122,10 +122,21 @@ __device__ __forceinline__ ffloat ff_frac_mul_int(int k, float d1, float d2, flo
 // W_a(t) = sum_i w_a,i Z_i(t) are the transforms of P_a (Sec. II.C projection applied before the
 // t_c scan instead of after it).
 // ------------------------------------------------------------------------------------------
+// Pass A's exchange padding: one spare element per 8 for 16-byte elements in radix-8 stages (their
+// first-stage writes would otherwise fall two to a bank group), per 16 otherwise.
+template <typename Real, int MAXRB>
+__host__ __device__ constexpr int pass_a_pad_shift() {
+    return sizeof(cplx<Real>) == 16 && MAXRB == 3 ? 3 : 4;
+}
+template <typename Real, int LOG_L, int K1B, int MAXRB>
+__host__ __device__ constexpr int pass_a_buf_elems() {
+    return K1B * xbuf_elems<pass_a_pad_shift<Real, MAXRB>()>(LOG_L);
+}
+
 // Pass A keeps two FFT exchange buffers when both fit in 200 KB of shared memory.
-template <typename Real, int LOG_L, int K1B>
+template <typename Real, int LOG_L, int K1B, int MAXRB>
 __host__ __device__ constexpr bool pass_a_pingpong() {
-    return 2 * sizeof(cplx<Real>) * (size_t)K1B * fft16_buf_elems(LOG_L) <= 200 * 1024;
+    return 2 * sizeof(cplx<Real>) * (size_t)pass_a_buf_elems<Real, LOG_L, K1B, MAXRB>() <= 200 * 1024;
 }
 
 // The float-float form reduces the chirp phase in binary64 (basis as in the binary64 form) and the
@@ -237,7 +248,8 @@ pass_a_kernel(const cplx<Real>* __restrict__ y, const Basis<phase_t<Real>>* __re
             if (FCAS_CHECK(((int64_t)blk * (L / 2) + j) * K1B + c + (int64_t)q * G * K1B < ((int64_t)L / 2 << log_n1),
                            kCheckBasis))
                 b = bb[(int64_t)q * G * K1B];
-            if (FCAS_CHECK(q * (int)blockDim.x + (int)threadIdx.x < K1B * fft16_buf_elems(LOG_L), kCheckExchangeWrite))
+            if (FCAS_CHECK((q * (int)blockDim.x + (int)threadIdx.x < pass_a_buf_elems<Real, LOG_L, K1B, MAXRB>()),
+                           kCheckExchangeWrite))
                 smem[q * blockDim.x + threadIdx.x] = ff_unit_phasor(chirp_frac(b, *pp), ptab);
         }
     }
@@ -329,8 +341,9 @@ pass_a_kernel(const cplx<Real>* __restrict__ y, const Basis<phase_t<Real>>* __re
         constexpr int NX = (LOG_L + MAXRB - 1) / MAXRB - 1;
         // FP32: stage twiddles mostly loaded (60-min pass A 4.11 -> 4.07 ms; pass B keeps the
         // products, which need fewer registers than its three CTAs per SM allow for the loads)
-        fftr<Real, +1, LOG_L, MAXRB, pass_a_pingpong<Real, LOG_L, K1B>(), 0, true, sizeof(Real) == 4>(
-            v, smem + c, K1B, j, stw, K1B * fft16_buf_elems(LOG_L), (a * NX) & 1);
+        fftr<Real, +1, LOG_L, MAXRB, pass_a_pingpong<Real, LOG_L, K1B, MAXRB>(), 0, true, sizeof(Real) == 4,
+             pass_a_pad_shift<Real, MAXRB>()>(v, smem + c, K1B, j, stw, pass_a_buf_elems<Real, LOG_L, K1B, MAXRB>(),
+                                              (a * NX) & 1);
         C* orow = out + ((p * kSeries + a) * L) * (int64_t)n1 + k1;
         // e^{2 pi i k1 ta / N} for ta = j + q G: the value at q = 0 times powers of the step e^{2 pi i k1 G / N}
         const int m0 = k1 * j, ms = k1 * G;   // < N
@@ -459,7 +472,8 @@ template <typename Real, int LG, int K1B, int MAXRB = 4>
 static cudaError_t pass_a_at(const FitnessPlan& pl, const ParticleParams* params, int64_t p0, int64_t np, void* inter,
                              cudaStream_t s) {
     constexpr int THREADS = K1B * ((1 << LG) / fftr_v(LG, MAXRB));
-    const size_t smem = (pass_a_pingpong<Real, LG, K1B>() ? 2 : 1) * sizeof(cplx<Real>) * (size_t)K1B * fft16_buf_elems(LG);
+    const size_t smem = (pass_a_pingpong<Real, LG, K1B, MAXRB>() ? 2 : 1) * sizeof(cplx<Real>) *
+                        (size_t)pass_a_buf_elems<Real, LG, K1B, MAXRB>();
     auto kern = pass_a_kernel<Real, LG, K1B, MAXRB>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
