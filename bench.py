@@ -9,6 +9,15 @@ its own data realisation and particle batch, no data-path collective).
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
 
 ``--impl reference`` times the FP64 CPU oracle on a bounded sample of the same workload.
+
+Besides the contract keys the line carries: ``roofline`` (pass A's algorithmic bytes over its
+CUDA-event time against the measured HBM copy rate, and its DRAM bytes from the committed ncu
+record when that was taken on the current kernel sources), ``alu_view`` (algorithmic flops against
+the FP32 issue peak), ``kernels`` (per-kernel times), ``fp64_form`` and ``ff_form`` (the binary64
+and float-float forms on the same particles, with their differences from the FP32 form and from
+each other), ``cufft_form`` (the straightforward cuFFT path), the PSO searches (``search``,
+``paper_config_search``, ``search_time_over_data_time``), ``batched_uneven``, the background and
+tiling studies, and ``cpu_baseline`` (the oracle on the host cores, N = 1 only).
 """
 
 import argparse
