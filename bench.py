@@ -16,8 +16,11 @@ record when that was taken on the current kernel sources), ``alu_view`` (algorit
 the FP32 issue peak), ``kernels`` (per-kernel times), ``fp64_form`` and ``ff_form`` (the binary64
 and float-float forms on the same particles, with their differences from the FP32 form and from
 each other), ``cufft_form`` (the straightforward cuFFT path), the PSO searches (``search``,
-``paper_config_search``, ``search_time_over_data_time``), ``batched_uneven``, the background and
-tiling studies, and ``cpu_baseline`` (the oracle on the host cores, N = 1 only).
+``paper_config_search``, ``search_60min`` and ``search_time_over_data_time``: the full 8 x 40 x 2000
+search on the 60-min data, timed in full), ``differentiation`` (FP32 adjoint-gradient throughput and
+gradient polishing), ``batched_uneven`` (64 segments of 15/30/60 min), the background and tiling
+studies, and ``cpu_baseline`` (the oracle on the host cores, N = 1 only; the same leg evaluates the
+oracle at the points the search and the polishing report).
 """
 
 import argparse
@@ -66,8 +69,11 @@ def parse():
                     help="timed batches of 4 particles of the cuFFT comparison form (0 = skip)")
     ap.add_argument("--no-search", action="store_true", help="skip the PSO search measurements")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shape (no autotuning)")
-    ap.add_argument("--group-segments", type=int, default=6,
+    ap.add_argument("--group-segments", type=int, default=64,
                     help="segments of the batched uneven-length measurement (0 = skip)")
+    ap.add_argument("--search-iters", type=int, default=2000,
+                    help="PSO iterations of the timed 60-min search (the search-time ratio)")
+    ap.add_argument("--no-gradient", action="store_true", help="skip the gradient and polishing measurements")
     return ap.parse_args()
 
 
@@ -362,7 +368,9 @@ def bench_ours(args, ranks):
         ff.update({"dtype": "f64 phase + float-float transforms",
                    "error_vs_fp64_form": form_error(fitff, tcff, fit64, tc64)})
 
-    search = None if args.no_search else bench_search(fc, ranks, data, w, dev)
+    search = None if args.no_search else bench_search(fc, ranks, data, w, dev, args.search_iters)
+    grad = None if (args.no_search or args.no_gradient) else bench_gradient(fc, ranks, dev,
+                                                                              search["best_64s"]["snr10"])
     group = None if args.group_segments <= 0 else bench_group(fc, ranks, args.group_segments, dev)
     background, tiled = (None, None) if args.background_slides <= 0 else bench_background(fc, ranks, dev,
                                                                                         args.background_slides)
@@ -391,12 +399,37 @@ def bench_ours(args, ranks):
                                        {"value": round(PSO_EVALS / value / DATA_SECONDS, 5),
                                         "how": "extrapolated: 8 runs x 40 particles x 2000 iterations / value / 3600 s"}),
         "search": search["search_64s"] if search else None,
+        "search_60min": search["search_60min"] if search else None,
+        "differentiation": grad,
         "batched_uneven": group, "background_time_slides": background, "tiled_search": tiled,
         "paper_config_search": paper_cfg,
         "paper_context": {"search_over_data": [1.4, 0.5], "hardware": "1 KNL node per PSO run, FP64"},
     }
     if ranks.rank == 0 and ranks.world == 1 and args.cpu_sample > 0:      # the CPU baseline is an N = 1 figure
-        out["cpu_baseline"] = cpu_baseline(w, ranks.rank, theta, args.cpu_sample)
+        judge = {}
+        if search:
+            judge["search_60min_best"] = (w.name, ranks.rank, {}, [search["search_60min"]["best_theta"]])
+        if grad:
+            pol = grad["polish"]
+            d = pol["data"]
+            judge["polish_before"] = (d["workload"], d["seed"], {"snr": d["snr"]}, pol["theta_before"])
+            judge["polish_after"] = (d["workload"], d["seed"], {"snr": d["snr"]}, pol["theta_after"])
+        out["cpu_baseline"] = cpu_baseline(w, ranks.rank, theta, args.cpu_sample, judge)
+        jv = out["cpu_baseline"].get("judged_by_oracle", {})
+        if "search_60min_best" in jv:
+            out["search_60min"]["oracle_fitness_at_best"] = jv["search_60min_best"][0][0]
+        if "polish_after" in jv:
+            before = np.array([v for v, _ in jv["polish_before"]])
+            after = np.array([v for v, _ in jv["polish_after"]])
+            out["differentiation"]["polish"]["oracle_gain"] = {
+                "fitness_before": [round(float(v), 4) for v in before],
+                "fitness_after": [round(float(v), 4) for v in after],
+                "gain": [round(float(v), 5) for v in after - before],
+                "mean_relative_gain": float(np.mean((after - before) / before)),
+                "how": "FP64 oracle fitness at each run's best particle before and after 10 fcas_polish steps"}
+    if grad:
+        for k in ("theta_before", "theta_after", "data"):
+            grad["polish"].pop(k, None)
     return out
 
 
@@ -515,13 +548,15 @@ def _pso_box(w):
     return (0.0, 2 * 3.141592653589793, -0.5 * 3.141592653589793, 0.5 * 3.141592653589793, t0lo, t0hi, t15lo, t15hi)
 
 
-def bench_search(fc, ranks, data60, w60, dev):
+def bench_search(fc, ranks, data60, w60, dev, iters60=2000):
     """Full PSO searches: 8 lbest-ring runs x 40 particles x 2000 iterations on the 64-s data (an SNR-10
-    and an SNR-12 injection and a noise-only realisation), and the same swarm on the 60-min data for
-    a reduced number of iterations, scaled linearly to 2000 (run time is linear in the iteration count)."""
+    and an SNR-12 injection and a noise-only realisation), and the same search on the 60-min data of
+    the fitness benchmark (SNR-10 injection), timed in full: its wall time over the 3600-s data
+    duration is the search-time ratio."""
     import torch
     w = sd.C1
     runs = []
+    best_64s = {}
     for kind, kw in (("snr10", dict(snr=10.0)), ("snr12", dict(snr=12.0)), ("noise", dict(inject=False))):
         data = sd.make_dataset(w, seed=10 + ranks.rank, **kw)
         ctx = fc.fcas_create(data["det"], data["psd"], data["data"], w.n_fft, w.fs, w.f_low, w.f_high)
@@ -532,6 +567,7 @@ def bench_search(fc, ranks, data60, w60, dev):
         res = fc.fcas_search(ctx, cfg)
         wall = time.perf_counter() - t
         best = max(res, key=lambda r: r["fitness"])
+        best_64s[kind] = res
         entry = {"realisation": kind, "wall_s": round(wall, 3), "wall_over_data": round(wall / (w.n_samples / w.fs), 4),
                  "evaluations": int(sum(r["evaluations"] for r in res)), "best_fitness": best["fitness"],
                  "best_theta": [round(v, 6) for v in best["theta"]], "best_tc_s": best["tc"] / w.fs}
@@ -539,21 +575,66 @@ def bench_search(fc, ranks, data60, w60, dev):
             entry["injected"] = _injected(fc, ctx, w, data["inj"])
         ctx.close()
         runs.append(entry)
-    # the 60-min segment
-    iters = 50
+    # the 60-min segment, all iterations timed
     ctx = fc.fcas_create(data60["det"], data60["psd"], data60["data"], w60.n_fft, w60.fs, w60.f_low, w60.f_high)
-    fc.fcas_search(ctx, fc.pso_config(n_runs=8, n_particles=40, n_iter=3, seed=1, box=_pso_box(w60)))
+    fc.fcas_autotune(ctx, 64)
+    fc.fcas_search(ctx, fc.pso_config(n_runs=8, n_particles=40, n_iter=3, seed=1, box=_pso_box(w60)))   # warm-up
     torch.cuda.synchronize(dev)
     t = time.perf_counter()
-    fc.fcas_search(ctx, fc.pso_config(n_runs=8, n_particles=40, n_iter=iters, seed=3, box=_pso_box(w60)))
+    res = fc.fcas_search(ctx, fc.pso_config(n_runs=8, n_particles=40, n_iter=iters60, seed=3 + ranks.rank,
+                                            box=_pso_box(w60)))
     wall = time.perf_counter() - t
+    best = max(res, key=lambda r: r["fitness"])
+    search60 = {"workload": w60.name, "runs": 8, "particles": 40, "iterations": iters60, "wall_s": round(wall, 3),
+                "evaluations": int(sum(r["evaluations"] for r in res)),
+                "evals_per_s": round(sum(r["evaluations"] for r in res) / wall, 1),
+                "best_fitness": best["fitness"], "best_theta": [round(v, 6) for v in best["theta"]],
+                "best_tc_s": best["tc"] / w60.fs, "run_best_fitness": [round(r["fitness"], 3) for r in res],
+                "injected": _injected(fc, ctx, w60, data60["inj"]) if data60["inj"] is not None else None}
     ctx.close()
-    scaled = wall * 2000.0 / iters
+    ratio = {"value": round(wall / DATA_SECONDS, 5),
+             "how": f"60-min data, 8 runs x 40 particles x {iters60} iterations, measured in full ({wall:.2f} s) "
+                    "/ 3600 s"}
     return {"search_64s": {"workload": w.name, "runs": 8, "particles": 40, "iterations": 2000, "realisations": runs},
-            "search_time_over_data_time": {"value": round(scaled / DATA_SECONDS, 5),
-                                           "how": f"60-min data, 8 runs x 40 particles: {iters} iterations measured "
-                                                  f"in {wall:.3f} s, scaled linearly to 2000 iterations",
-                                           "search_s_2000_iterations": round(scaled, 2)}}
+            "search_60min": search60, "search_time_over_data_time": ratio, "best_64s": best_64s}
+
+
+def bench_gradient(fc, ranks, dev, best_runs, steps=5):
+    """Differentiation form (64-s data): the adjoint gradient of 320 particles in the FP32 form, timed
+    on the device, and 10 steps of gradient polishing (fcas_polish) of each PSO run's best particle of
+    the SNR-10 search. The polished points are judged by the FP64 oracle in the CPU-baseline leg."""
+    import torch
+    w = sd.C1
+    data = sd.make_dataset(w, seed=10 + ranks.rank, snr=10.0)
+    ctx = fc.fcas_create(data["det"], data["psd"], data["data"], w.n_fft, w.fs, w.f_low, w.f_high)
+    th = torch.tensor(sd.make_particles(w, 320, seed=1), device=dev)
+    fit, tc = fc.fcas_fitness(ctx, th)
+    grad = torch.empty((320, 4), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(3):
+        fc.fcas_gradient(ctx, th, tc, grad, stream=stream.cuda_stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fc.fcas_gradient(ctx, th, tc, grad, stream=stream.cuda_stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    sec = e0.elapsed_time(e1) / 1e3
+    start = np.array([r["theta"] for r in best_runs])
+    f0, _ = fc.fcas_fitness(ctx, start)
+    torch.cuda.synchronize(dev)
+    t = time.perf_counter()
+    th_p, f_p, tc_p, acc = fc.fcas_polish(ctx, start, steps=10)
+    polish_s = time.perf_counter() - t
+    ctx.close()
+    return {"gradient": {"workload": w.name, "particles": 320, "precision": "fp32",
+                         "value": round(320 * steps / sec, 1), "unit": "gradients/s",
+                         "ms_per_call": round(1e3 * sec / steps, 3)},
+            "polish": {"workload": w.name, "points": len(start), "steps": 10, "wall_s": round(polish_s, 4),
+                       "fitness_before": [round(float(v), 4) for v in f0],
+                       "fitness_after": [round(float(v), 4) for v in f_p], "accepted_steps": [int(a) for a in acc],
+                       "theta_before": start.tolist(), "theta_after": th_p.tolist(),
+                       "data": {"workload": w.name, "seed": 10 + ranks.rank, "snr": 10.0}}}
 
 
 def bench_background(fc, ranks, dev, n_slides):
@@ -638,28 +719,50 @@ def _injected(fc, ctx, w, inj):
             "fitness_at_injection": float(f[0]), "tc_s_at_injection": float(t[0]) / w.fs}
 
 
+def _segment_workload(seg, rng_draws):
+    """Segment seg of the uneven-length batch: durations cycled over 15/30/60 min at 2048 Hz (FFT
+    lengths 2^21, 2^22, 2^23), masses and SNR from the given draws (m1, m2, snr)."""
+    minutes, n_fft = ((15, 1 << 21), (30, 1 << 22), (60, 1 << 23))[seg % 3]
+    n_samples = minutes * 60 * 2048
+    m1, m2, snr = rng_draws
+    return dataclasses.replace(sd.C2, name=f"{minutes}min", n_samples=n_samples, n_fft=n_fft, m1=float(m1),
+                               m2=float(m2), snr=float(snr), arrival_s=n_samples / 2048.0 / 3.0)
+
+
+def _segment_data(args):
+    """Worker of the segment data pool: the seeded data of one segment (data and detector table)."""
+    seg, draws, seed = args
+    d = sd.make_dataset(_segment_workload(seg, draws), seed=seed)
+    return seg, d["data"], d["det"]
+
+
 def bench_group(fc, ranks, n_seg, dev, iters=5):
     """Uneven batching: n_seg noise realisations with DNS injections (SNR ~ U[10, 14], masses ~ U[1, 3]
     Msun, random sky), durations cycled over 15/30/60 min at 2048 Hz (FFT lengths 2^21, 2^22, 2^23),
     every segment's swarm (8 runs x 40 particles) advanced together, one graph launch per iteration,
-    each segment with autotuned launch shapes."""
+    each segment with autotuned launch shapes and the library's analytic PSD (psd = NULL). The seeded
+    data of the segments is generated by a pool of spawned host processes."""
+    import multiprocessing as mp
     import tempfile
     import torch
     rng = np.random.default_rng(4000 + ranks.rank)
+    draws = [(*rng.uniform(1.0, 3.0, 2), rng.uniform(10.0, 14.0)) for _ in range(n_seg)]
     cache = os.path.join(tempfile.gettempdir(), f"fcas_tune_rank{ranks.rank}.txt")
-    ctxs, lengths = [], []
-    for s_ in range(n_seg):
-        minutes, n_fft = ((15, 1 << 21), (30, 1 << 22), (60, 1 << 23))[s_ % 3]
-        n_samples = minutes * 60 * 2048
-        m1, m2 = rng.uniform(1.0, 3.0, 2)
-        w = dataclasses.replace(sd.C2, name=f"{minutes}min", n_samples=n_samples, n_fft=n_fft, m1=m1, m2=m2,
-                                snr=float(rng.uniform(10.0, 14.0)), arrival_s=n_samples / 2048.0 / 3.0)
-        d = sd.make_dataset(w, seed=500 + 64 * ranks.rank + s_)
-        ctx = fc.fcas_create(d["det"], d["psd"], d["data"], w.n_fft, w.fs, w.f_low, w.f_high,
-                             flags=fc.FCAS_SETUP_LAZY_SCRATCH)
-        fc.fcas_autotune(ctx, 64, cache)
-        ctxs.append(ctx)
-        lengths.append(n_fft)
+    ctxs, lengths = [None] * n_seg, [0] * n_seg
+    workers = max(1, min(n_seg, os.cpu_count() or 1, 16))
+    avail = _mem_available_bytes()
+    if avail:
+        workers = max(1, min(workers, int(avail * 0.4 // 2.5e9)))
+    t_data = time.perf_counter()
+    jobs = [(s_, draws[s_], 500 + 64 * ranks.rank + s_) for s_ in range(n_seg)]
+    with mp.get_context("spawn").Pool(workers) as pool:
+        for s_, data, det in pool.imap_unordered(_segment_data, jobs):
+            w = _segment_workload(s_, draws[s_])
+            ctx = fc.fcas_create(det, None, data, w.n_fft, w.fs, w.f_low, w.f_high, flags=fc.FCAS_SETUP_LAZY_SCRATCH)
+            fc.fcas_autotune(ctx, 64, cache)
+            ctxs[s_], lengths[s_] = ctx, w.n_fft
+            del data
+    prep_s = time.perf_counter() - t_data
     cfg = lambda it: fc.pso_config(n_runs=8, n_particles=40, n_iter=it, seed=7, box=_pso_box(sd.C2))
     with fc.fcas_group_create(ctxs) as grp:
         grp.search(cfg(2))                      # warm-up (also builds the iteration graph once)
@@ -672,9 +775,11 @@ def bench_group(fc, ranks, n_seg, dev, iters=5):
         c.close()
     evals = sum(r["evaluations"] for seg in res for r in seg)
     return {"segments": n_seg, "fft_lengths": lengths, "runs_per_segment": 8, "particles": 40, "iterations": iters,
-            "wall_s": round(wall, 4), "s_per_iteration": round(wall / iters, 5),
-            "evals_per_s": round(evals / wall, 1), "evaluations": int(evals),
-            "shapes": [{k: i[k] for k in ("n_fft", "split_bias", "k1b", "sub")} for i in shapes]}
+            "evaluations_per_iteration": int(evals // iters), "wall_s": round(wall, 4),
+            "s_per_iteration": round(wall / iters, 5), "evals_per_s": round(evals / wall, 1),
+            "evaluations": int(evals), "data_and_contexts_s": round(prep_s, 2), "data_workers": workers,
+            "psd": "analytic aLIGO fit evaluated by the library (psd = NULL)",
+            "shapes": [{k: i[k] for k in ("n_fft", "split_bias", "k1b", "sub")} for i in shapes[:3]]}
 
 
 def _oracle_worker(wname, seed, thetas, barrier, queue):
@@ -751,15 +856,37 @@ def oracle_pool(w, seed, theta, steps):
     return n, step_s
 
 
-def cpu_baseline(w, seed, theta, steps):
+def oracle_judgements(judge):
+    """Part of the CPU-baseline leg: the FP64 oracle's fitness (and argmax) at points the GPU legs
+    report, each on its own seeded workload. judge: {name: (workload name, seed, make_dataset
+    keywords, [theta, ...])}."""
+    from oracle import fcas_oracle as o
+    out = {}
+    setups = {}
+    for name, (wname, seed, kw, thetas) in judge.items():
+        key = (wname, seed, tuple(sorted(kw.items())))
+        if key not in setups:
+            w = sd.workload_by_name(wname)
+            data = sd.make_dataset(w, seed=seed, **kw)
+            setups[key] = o.OracleSetup(data["det"], data["psd"], data["data"], w.n_fft, w.fs, w.f_low, w.f_high)
+        out[name] = [list(o.fitness(setups[key], np.asarray(th, dtype=np.float64))) for th in thetas]
+    return out
+
+
+def cpu_baseline(w, seed, theta, steps, judge=None):
     n, step_s = oracle_pool(w, seed, theta, steps)
     value = n * steps / sum(step_s)
-    return {"value": round(value, 4), "unit": UNIT, "cores": n, "kind": "oracle",
-            "sample": f"{n * steps} particles of the same workload ({steps} per core), FP64 numpy oracle, "
-                      f"{n} single-threaded processes, data preparation excluded",
-            "s_per_eval_per_core": round(n / value, 3),
-            "search_s_extrapolated": {"value": round(PSO_EVALS / value, 1),
-                                      "how": "8 runs x 40 particles x 2000 iterations / value (extrapolated, not run)"}}
+    out = {"value": round(value, 4), "unit": UNIT, "cores": n, "kind": "oracle",
+           "sample": f"{n * steps} particles of the same workload ({steps} per core), FP64 numpy oracle, "
+                     f"{n} single-threaded processes, data preparation excluded",
+           "s_per_eval_per_core": round(n / value, 3),
+           "search_s_extrapolated": {"value": round(PSO_EVALS / value, 1),
+                                     "how": "8 runs x 40 particles x 2000 iterations / value (extrapolated, not run)"}}
+    if judge:
+        t = time.perf_counter()
+        out["judged_by_oracle"] = oracle_judgements(judge)
+        out["judge_s"] = round(time.perf_counter() - t, 2)
+    return out
 
 
 def bench_reference(args, ranks):

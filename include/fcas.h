@@ -21,6 +21,8 @@
  *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
  *  - The caller keeps ownership of every buffer it passes; the context owns everything it
  *    allocates. A context must not be used from two threads at once.
+ *  - A context belongs to the CUDA device that was current when it was created: every call that
+ *    takes it must be made with that device current (FCAS_ERR_INVALID otherwise).
  *  - All floating-point inputs are IEEE binary64.
  */
 #ifndef FCAS_H
@@ -83,7 +85,10 @@ typedef struct fcas_ctx fcas_ctx;
  * fcas_create -- prepare a data segment (Sec. II.D).
  *   setup : segment description (host).
  *   det   : [n_det] detector geometry (host).
- *   psd   : [n_det][n_fft/2+1] one-sided PSD S_n^i(f_k), f_k = k fs / n_fft (host or device).
+ *   psd   : [n_det][n_fft/2+1] one-sided PSD S_n^i(f_k), f_k = k fs / n_fft (host or device), or
+ *           NULL for the analytic fit to the aLIGO design sensitivity for every detector (Sec. II.A
+ *           noise model), S(f) = 1e-49 [x^-4.14 - 5 x^-2 + 111 (1 - x^2 + x^4/2) / (1 + x^2/2)],
+ *           x = f / 215 Hz, evaluated in binary64 on the device.
  *           Only bins with f_low < f_k <= f_high, 0 < k < n_fft/2 are read; they must be finite and > 0.
  *   data  : [n_det][n_samples] real strain time series x^i (host or device).
  * The segment is zero-padded to n_fft, transformed (x~[k] = dt sum_n x[n] e^{-2 pi i k n/N}),
@@ -132,22 +137,28 @@ int fcas_fitness(fcas_ctx* ctx, int64_t n, const double* theta, double* fitness,
  * routine.
  *
  * Its scratch (per-particle parameters, the intermediate transform between the two FFT passes and
- * the argmax partials) lives in one static device array of 32 MiB inside libfcas.so, which every
- * GPU that loads the library holds until the process exits. One particle needs
- * 2 * n_fft * (8 bytes FP32, 16 bytes FP64) plus ~0.5 KB; particles are processed in chunks
- * that fit. A context whose single particle does not fit (n_fft >= 2^21 in FP32, >= 2^20 in FP64)
- * is rejected with FCAS_ERR_INVALID and a message naming the sizes.
+ * the argmax partials) lives in one static device array of 32 MiB inside libfcas.so. The array
+ * belongs to the library's no-alloc module, which CUDA loads on a device lazily: the first call of
+ * this entry point on a device loads it there, and that load allocates the 32 MiB, which the device
+ * then holds until the process exits. Make that first call during the caller's set-up phase, with
+ * the context's device current and before any stream capture; from then on the call allocates
+ * nothing. One particle needs 2 * n_fft * (8 bytes FP32, 16 bytes FP64 and float-float) plus
+ * ~0.5 KB; particles are processed in chunks that fit. A context whose single particle does not fit
+ * (n_fft >= 2^21 in FP32, >= 2^20 in the other forms) is rejected with FCAS_ERR_INVALID and a
+ * message naming the sizes.
  *
- *   ctx, n, theta, fitness, tc : as for fcas_fitness, except that theta, fitness and tc must be
- *                                device pointers (host arrays would need staging memory):
- *                                FCAS_ERR_INVALID otherwise.
- *   stream                     : as for fcas_fitness; the call is asynchronous on it.
- *
- * The first call on a device looks up the device address of the scratch array (once per device,
- * with that device current); make that first call before any stream capture. Every call, from every
- * context and thread, shares the one array and leaves its contents behind; nothing in it needs to
- * start at zero because each call writes every word it reads. Calls that overlap on the GPU
- * (different streams, or different host threads) race on the array: serialise them.
+ *   ctx, n, theta, fitness, tc : as for fcas_fitness, except that theta [n][4], fitness [n] and
+ *                                tc [n] must be device memory of the current device (host arrays
+ *                                would need staging memory): FCAS_ERR_INVALID otherwise. The
+ *                                library cannot see the arrays' sizes: the caller guarantees them.
+ *   stream                     : a stream of the current device, as for fcas_fitness; the call is
+ *                                asynchronous on it.
+ * The context's device must be current (FCAS_ERR_INVALID otherwise, as for every entry point that
+ * takes a context). The first call on a device also looks up the device address of the scratch
+ * array (once per device, with that device current). Every call, from every context and thread,
+ * shares the one array and leaves its contents behind; nothing in it needs to start at zero because
+ * each call writes every word it reads. Calls that overlap on the GPU (different streams, or
+ * different host threads) race on the array: serialise them.
  */
 int fcas_fitness_noalloc(const fcas_ctx* ctx, int64_t n, const double* theta, double* fitness, int64_t* tc,
                          void* stream);
@@ -251,6 +262,28 @@ int fcas_search(fcas_ctx* ctx, const fcas_pso_config* cfg, fcas_search_result* r
 int fcas_gradient(fcas_ctx* ctx, int64_t n, const double* theta, const int64_t* tc, double* grad, void* stream);
 
 /*
+ * fcas_polish -- gradient polishing of a batch of points (the differentiation form: a few ascent
+ * steps along the adjoint gradient of fcas_gradient, e.g. on the best particle of each PSO run of
+ * Sec. III; the paper's own search has no such step). Per particle and step, with
+ * s = scales * (1, 1, tau0, tau1.5) (absolute step scales for the angles, relative ones for the chirp
+ * times), the direction is d = s^2 g / |s g| for the gradient g at the current point and its argmax
+ * t_c; trial points theta + l d with l = 1, 1/2, 1/4, ... (at most max_halvings trials) are evaluated
+ * with the context's fitness, and the first trial that raises the fitness is taken. A particle whose
+ * gradient is not finite, or whose trials all fail, keeps its point for that step.
+ *   theta    : [n][4] in: starting points, out: polished points (host or device).
+ *   fitness  : [n] out: fitness at the polished points (host or device).
+ *   tc       : [n] out: their argmax sample index (host or device).
+ *   steps    : ascent steps (>= 0; 0 only evaluates the fitness).
+ *   scales   : host [4] step scales (finite, > 0), or NULL for (1e-2 rad, 1e-2 rad, 1e-4, 1e-4).
+ *   max_halvings : trial points per step (>= 1).
+ *   accepted : [n] out: accepted steps per particle (host or device), or NULL.
+ * Synchronous. Every evaluation, gradient, trial and acceptance runs on the device; the host only
+ * reads, after each round of trials, how many particles are still searching.
+ */
+int fcas_polish(fcas_ctx* ctx, int64_t n, double* theta, double* fitness, int64_t* tc, int32_t steps,
+                const double* scales, int32_t max_halvings, int32_t* accepted, void* stream);
+
+/*
  * fcas_autotune -- choose the launch shapes of the fitness path for this context by timing them:
  * the N = n1 n2 split (balanced, or a pass-A transform half as long), the number of columns per
  * pass-A CTA among the compiled widths, pass A's stage radix (16, or 8 with twice the threads),
@@ -274,9 +307,9 @@ typedef struct fcas_group fcas_group;
 /*
  * fcas_set_shape -- pin the launch shape without timing: split_bias 0 or 1, k1b one of the compiled
  * pass-A widths for the resulting length (0 = default), sub a power of two, radix_bits_a 4 (radix-16
- * stages), 3 (radix-8 stages for 2^10..2^12-point columns: FP32 form with k1b = 4, float-float form
- * with k1b = 2) or 0 (the default of the form and length: radix 8 for the float-float form's
- * 2^11-point columns, radix 16 otherwise).
+ * stages), 3 (radix-8 stages, float-float form only, for 2^10..2^12-point columns with k1b = 2) or 0
+ * (the default of the form and length: radix 8 for the float-float form's 2^11-point columns, radix 16
+ * otherwise).
  * FCAS_ERR_INVALID for a shape that is not available. Synchronous.
  */
 int fcas_set_shape(fcas_ctx* ctx, int32_t split_bias, int32_t k1b, int32_t sub, int32_t radix_bits_a, void* stream);

@@ -13,10 +13,12 @@ Every step is the paper's definition written out in numpy float64, evaluated nai
   * precomputed template norms, data-side time shift, over-whitening -- Sec. II.D,
     eq. data_template_innprod
 
-Readings where the paper is silent (each listed in the design notes):
+Readings taken where the paper is silent, ambiguous or garbled (each fixed here, with its reason):
   * Gamma^2 = 2 max lambda = X^T M^{-1} X, so that a noiseless injection at the true parameters
-    gives the network SNR^2 of eq. optimalSNR.
-  * delta is a latitude in [-pi/2, pi/2]; n = (cos d cos a, cos d sin a, sin d).
+    gives the network SNR^2 of eq. optimalSNR (Sec. V compares thresholds of 9.3-9.5 with SNRs of
+    9-15, which puts the statistic on the SNR scale).
+  * delta is a latitude in [-pi/2, pi/2] (Sec. V's source positions have negative delta);
+    n = (cos d cos a, cos d sin a, sin d).
   * Delta^i = -n.r_i / c (eq. detresponse: h^i(t + Delta^i) = F h(t)).
   * The template is zero for f <= f_* (= f_low) and for f > f_high; bins 0 and N/2 are excluded.
   * t_c is the formal TaylorF2 coalescence time at the ECEF origin on the sample grid, the IFFT

@@ -5,7 +5,8 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
 PSO as used by the paper (Sec. III): particles move in a search box under a social and a
 cognitive attraction, lbest topology on a ring of particle indices, a fixed number of iterations,
 best-of-M independent runs with independent random streams. The paper defers the remaining
-details to earlier work; the readings taken here (listed in the design notes):
+details to earlier work; the readings taken here (the standard settings of that earlier lbest
+PSO work, stated in full so that the device code can be checked against them):
 
   * positions normalised to [0, 1]^4; alpha = 2 pi x0, delta = pi (x1 - 1/2),
     tau0 = lo + (hi - lo) x2, tau1.5 = lo + (hi - lo) x3;

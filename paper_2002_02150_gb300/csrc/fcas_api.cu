@@ -65,6 +65,33 @@ int report_error(int code, const char* msg) {
     g_last_error = msg;
     return code;
 }
+
+int check_ctx_device(const fcas_ctx* c, const char* fn) {
+    int dev = -1;
+    const cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(FCAS_ERR_CUDA, "%s: cudaGetDevice: %s", fn, cudaGetErrorString(e));
+    if (dev != c->device)
+        return fail(FCAS_ERR_INVALID, "%s: the context was created on device %d but device %d is current", fn,
+                    c->device, dev);
+    return FCAS_OK;
+}
+
+int check_device_array(const void* p, const char* fn, const char* what) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(FCAS_ERR_CUDA, "%s: cudaGetDevice: %s", fn, cudaGetErrorString(e));
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(FCAS_ERR_INVALID, "%s: %s is not a CUDA pointer", fn, what);
+    }
+    if (a.type == cudaMemoryTypeManaged) return FCAS_OK;
+    if (a.type != cudaMemoryTypeDevice)
+        return fail(FCAS_ERR_INVALID, "%s: %s must be device memory (host arrays would need staging memory)", fn, what);
+    if (a.device != dev)
+        return fail(FCAS_ERR_INVALID, "%s: %s lives on device %d but device %d is current", fn, what, a.device, dev);
+    return FCAS_OK;
+}
 }  // namespace fcas
 
 namespace {
@@ -74,7 +101,7 @@ void free_ctx(fcas_ctx* c) {
                     c->d_tw32, c->d_twlo32, c->d_twhi32, c->d_stw_a64, c->d_stw_a32, c->d_stw_b64, c->d_stw_b32,
                     c->d_twloff, c->d_twhiff, c->d_stw_aff, c->d_stw_bff, c->d_phff,
                     c->d_params, c->d_theta, c->d_fit, c->d_tc, c->d_inter, c->d_partials, c->d_pso,
-                    c->d_gsums, c->d_gstage, c->d_ynat};
+                    c->d_gsums, c->d_gstage, c->d_ynat, c->d_polish};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->search_stream) cudaStreamDestroy(c->search_stream);
@@ -181,6 +208,40 @@ cudaError_t launch_passes(fcas_ctx* c, int64_t n, double* d_fit, int64_t* d_tc, 
     return launch_passes_with(c, c->d_params, c->d_inter, c->d_partials, c->chunk, n, d_fit, d_tc, st);
 }
 
+// Per-particle buffers of the adjoint: band sums and a staging array for host outputs.
+int ensure_grad(fcas_ctx* c, int64_t n) {
+    if (n <= c->grad_cap) return FCAS_OK;
+    if (c->d_gsums) cudaFree(c->d_gsums);
+    if (c->d_gstage) cudaFree(c->d_gstage);
+    c->d_gsums = nullptr;
+    c->d_gstage = nullptr;
+    c->grad_cap = 0;
+    int rc = dev_alloc(&c->d_gsums, sizeof(double) * 12 * (size_t)c->setup.n_det * n, "gradient sums");
+    if (!rc) rc = dev_alloc(&c->d_gstage, sizeof(double) * 4 * (size_t)n, "gradient staging");
+    if (rc) return rc;
+    c->grad_cap = n;
+    return FCAS_OK;
+}
+
+// d Gamma^2 / d theta at fixed tc for n particles given on the device: geometry into the context's
+// particle parameters, the band sums, then their binary64 combination (needs ensure_particles and
+// ensure_grad for n).
+cudaError_t gradient_device(fcas_ctx* c, int64_t n, const double* d_theta, const int64_t* d_tc, double* d_grad,
+                            cudaStream_t st) {
+    cudaError_t e = launch_geometry(d_theta, n, c->d_params, c->d_det, c->d_sigma2s, c->setup.n_det, c->setup.f_low,
+                                    c->df, st);
+    if (e != cudaSuccess) return e;
+    const FitnessPlan plan = make_plan(c);
+    if (c->setup.precision == FCAS_PREC_FP32)
+        e = launch_grad_sums<float>(plan, c->k1b, c->k_lo, c->k_hi, c->d_params, d_tc, n, c->d_gsums, st);
+    else
+        e = launch_grad_sums<double>(plan, c->k1b, c->k_lo, c->k_hi, c->d_params, d_tc, n, c->d_gsums, st,
+                                     c->setup.precision == FCAS_PREC_FF);
+    if (e != cudaSuccess) return e;
+    return launch_grad_final(d_theta, d_tc, n, c->d_gsums, c->d_det, c->d_sigma2s, c->setup.n_det, c->setup.f_low,
+                             c->df, d_grad, st);
+}
+
 // Scratch of the fitness path (allocated at create unless FCAS_SETUP_LAZY_SCRATCH, else on first use).
 int ensure_scratch(fcas_ctx* c) {
     if (c->d_inter) return FCAS_OK;
@@ -197,7 +258,7 @@ int apply_layout(fcas_ctx* c, int bias, int k1b, int sub, int radix_bits_a, cuda
     const int l2 = split_log_n2_with(log_n, bias);
     const int l1 = log_n - l2;
     if (l1 > kMaxLogPass) return fail(FCAS_ERR_INVALID, "split bias %d gives a %d-point pass", bias, 1 << l1);
-    int ks[4];
+    int ks[8];
     const int nk = pass_a_k1b_variants(l2, c->setup.precision, ks);
     if (nk <= 0) return fail(FCAS_ERR_INVALID, "no pass-A shape for 2^%d-point columns", l2);
     if (k1b == 0) k1b = ks[0];
@@ -266,7 +327,7 @@ namespace {
 int create_impl(fcas_ctx** out, const fcas_setup* setup, const fcas_detector* det, const double* psd,
                 const double* data, const int64_t* shifts, void* stream) {
     g_last_error.clear();
-    if (!out || !setup || !det || !psd || !data) return fail(FCAS_ERR_INVALID, "fcas_create: NULL argument");
+    if (!out || !setup || !det || !data) return fail(FCAS_ERR_INVALID, "fcas_create: NULL argument");
     *out = nullptr;
     const fcas_setup& s = *setup;
     if (s.n_det < 1 || s.n_det > FCAS_MAX_DET)
@@ -309,8 +370,14 @@ int create_impl(fcas_ctx** out, const fcas_setup* setup, const fcas_detector* de
     if (k_hi < k_lo) return fail(FCAS_ERR_INVALID, "the band (f_low, f_high] contains no frequency bin");
 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int device = -1;
+    if (cudaGetDevice(&device) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(FCAS_ERR_CUDA, "fcas_create: no usable CUDA device");
+    }
     fcas_ctx* c = new fcas_ctx();
     c->setup = s;
+    c->device = device;
     c->log_n = log_n;
     c->log_n2 = split_log_n2_with(log_n, FCAS_SPLIT_BIAS);
     c->log_n1 = log_n - c->log_n2;
@@ -351,12 +418,15 @@ int create_impl(fcas_ctx** out, const fcas_setup* setup, const fcas_detector* de
         if (e_ != cudaSuccess) return cleanup(fail(FCAS_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_))); \
     } while (0)
 
-    // inputs on the device
+    // inputs on the device (psd = NULL: the analytic aLIGO fit, evaluated on the band bins)
     if (psd_dev) {
         d_psd = const_cast<double*>(psd);
     } else {
         FCAS_TRY(dev_alloc(&d_psd, sizeof(double) * (size_t)D * psd_row, "psd"));
-        FCAS_TRYCUDA(cudaMemcpyAsync(d_psd, psd, sizeof(double) * (size_t)D * psd_row, cudaMemcpyHostToDevice, st));
+        if (psd)
+            FCAS_TRYCUDA(cudaMemcpyAsync(d_psd, psd, sizeof(double) * (size_t)D * psd_row, cudaMemcpyHostToDevice, st));
+        else
+            FCAS_TRYCUDA(launch_analytic_psd(d_psd, D, psd_row, k_lo, k_hi, c->df, st));
     }
     if (data_dev) {
         d_data = const_cast<double*>(data);
@@ -487,6 +557,7 @@ int fcas_fitness(fcas_ctx* c, int64_t n, const double* theta, double* fitness, i
     if (!c) return fail(FCAS_ERR_INVALID, "fcas_fitness: NULL context");
     if (n < 0) return fail(FCAS_ERR_INVALID, "fcas_fitness: n < 0");
     if (n == 0) return FCAS_OK;
+    if (int rc0 = check_ctx_device(c, "fcas_fitness")) return rc0;
     if (!theta || !fitness || !tc) return fail(FCAS_ERR_INVALID, "fcas_fitness: NULL array");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const bool th_dev = is_device_ptr(theta), f_dev = is_device_ptr(fitness), t_dev = is_device_ptr(tc);
@@ -611,6 +682,7 @@ int fcas_search(fcas_ctx* c, const fcas_pso_config* cfg, fcas_search_result* res
     NvtxRange nvtx_("fcas_search");
     g_last_error.clear();
     if (!c || !results) return fail(FCAS_ERR_INVALID, "fcas_search: NULL argument");
+    if (int rc0 = check_ctx_device(c, "fcas_search")) return rc0;
     char msg[256];
     int rc = pso_validate(cfg, msg, sizeof(msg));
     if (rc) return fail(rc, "fcas_search: %s", msg);
@@ -656,6 +728,7 @@ int fcas_autotune(fcas_ctx* c, int64_t n_particles, const char* cache_path, void
     NvtxRange nvtx_("fcas_autotune");
     g_last_error.clear();
     if (!c) return fail(FCAS_ERR_INVALID, "fcas_autotune: NULL context");
+    if (int rc0 = check_ctx_device(c, "fcas_autotune")) return rc0;
     if (n_particles < 1) return fail(FCAS_ERR_INVALID, "fcas_autotune: n_particles < 1");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int dev = 0;
@@ -666,7 +739,7 @@ int fcas_autotune(fcas_ctx* c, int64_t n_particles, const char* cache_path, void
     for (char& ch : gpu)
         if (ch == ' ') ch = '_';
     char key[512];
-    snprintf(key, sizeof(key), "fcas-tune-v2 %s %lld %d %d %lld", gpu.c_str(), (long long)c->setup.n_fft,
+    snprintf(key, sizeof(key), "fcas-tune-v3 %s %lld %d %d %lld", gpu.c_str(), (long long)c->setup.n_fft,
              c->setup.n_det, c->setup.precision, (long long)n_particles);
     if (cache_path) {
         if (FILE* f = fopen(cache_path, "r")) {
@@ -714,8 +787,8 @@ int fcas_autotune(fcas_ctx* c, int64_t n_particles, const char* cache_path, void
         const int l2 = split_log_n2_with(c->log_n, bias);
         if (l2 == last_l2 || c->log_n - l2 > kMaxLogPass) continue;
         last_l2 = l2;
-        int ks[5], rbs[5];
-        int nk = pass_a_k1b_variants(l2, c->setup.precision, ks);   // at most 3
+        int ks[8], rbs[8];
+        int nk = pass_a_k1b_variants(l2, c->setup.precision, ks);   // at most 4, plus 2 radix-8 shapes below
         for (int q = 0; q < nk; ++q) rbs[q] = 4;
         for (int k8 : {4, 2}) {
             if (pass_a_radix8_available(l2, c->setup.precision, k8)) {
@@ -769,6 +842,7 @@ int fcas_autotune(fcas_ctx* c, int64_t n_particles, const char* cache_path, void
 int fcas_set_shape(fcas_ctx* c, int32_t split_bias, int32_t k1b, int32_t sub, int32_t radix_bits_a, void* stream) {
     g_last_error.clear();
     if (!c) return fail(FCAS_ERR_INVALID, "fcas_set_shape: NULL context");
+    if (int rc0 = check_ctx_device(c, "fcas_set_shape")) return rc0;
     if (split_bias < 0 || split_bias > 1) return fail(FCAS_ERR_INVALID, "fcas_set_shape: split_bias must be 0 or 1");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (radix_bits_a == 0) radix_bits_a = pass_a_default_radix_bits(split_log_n2_with(c->log_n, split_bias),
@@ -805,6 +879,7 @@ int fcas_group_create(fcas_group** out, int32_t n_ctx, fcas_ctx* const* ctxs, in
     int64_t nb = 0;
     for (int i = 0; i < n_ctx; ++i) {
         if (!ctxs[i]) return fail(FCAS_ERR_INVALID, "fcas_group_create: context %d is NULL", i);
+        if (int rc0 = check_ctx_device(ctxs[i], "fcas_group_create")) return rc0;
         const size_t b = inter_bytes_per_particle(ctxs[i]->setup.precision, ctxs[i]->setup.n_fft);
         if (b > inter_pp) inter_pp = b;
         if (ctxs[i]->nb_cap > nb) nb = ctxs[i]->nb_cap;
@@ -837,6 +912,8 @@ int fcas_group_search_boxes(fcas_group* g, const fcas_pso_config* cfg, const dou
     NvtxRange nvtx_("fcas_group_search");
     g_last_error.clear();
     if (!g || !results) return fail(FCAS_ERR_INVALID, "fcas_group_search: NULL argument");
+    for (const fcas_ctx* c : g->ctxs)
+        if (int rc0 = check_ctx_device(c, "fcas_group_search")) return rc0;
     char msg[256];
     int rc = pso_validate(cfg, msg, sizeof(msg));
     if (rc) return fail(rc, "fcas_group_search: %s", msg);
@@ -945,25 +1022,16 @@ int fcas_gradient(fcas_ctx* c, int64_t n, const double* theta, const int64_t* tc
     if (!c) return fail(FCAS_ERR_INVALID, "fcas_gradient: NULL context");
     if (n < 0) return fail(FCAS_ERR_INVALID, "fcas_gradient: n < 0");
     if (n == 0) return FCAS_OK;
+    if (int rc0 = check_ctx_device(c, "fcas_gradient")) return rc0;
     if (!theta || !tc || !grad) return fail(FCAS_ERR_INVALID, "fcas_gradient: NULL array");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const bool th_dev = is_device_ptr(theta), tc_dev = is_device_ptr(tc), g_dev = is_device_ptr(grad);
     int rc = ensure_particles(c, n);
+    if (!rc) rc = ensure_grad(c, n);
     if (rc) return rc;
     if (!th_dev || !tc_dev) {
         rc = ensure_staging(c, n);
         if (rc) return rc;
-    }
-    if (n > c->grad_cap) {
-        if (c->d_gsums) cudaFree(c->d_gsums);
-        if (c->d_gstage) cudaFree(c->d_gstage);
-        c->d_gsums = nullptr;
-        c->d_gstage = nullptr;
-        c->grad_cap = 0;
-        rc = dev_alloc(&c->d_gsums, sizeof(double) * 12 * (size_t)c->setup.n_det * n, "gradient sums");
-        if (!rc) rc = dev_alloc(&c->d_gstage, sizeof(double) * 4 * (size_t)n, "gradient staging");
-        if (rc) return rc;
-        c->grad_cap = n;
     }
     const double* d_theta = theta;
     if (!th_dev) {
@@ -976,21 +1044,101 @@ int fcas_gradient(fcas_ctx* c, int64_t n, const double* theta, const int64_t* tc
         d_tc = c->d_tc;
     }
     double* d_grad = g_dev ? grad : c->d_gstage;
-    FCAS_CUDA(launch_geometry(d_theta, n, c->d_params, c->d_det, c->d_sigma2s, c->setup.n_det, c->setup.f_low, c->df,
-                              st));
-    const FitnessPlan plan = make_plan(c);
-    const int k1b = c->k1b;
-    if (c->setup.precision == FCAS_PREC_FP32)
-        FCAS_CUDA(launch_grad_sums<float>(plan, k1b, c->k_lo, c->k_hi, c->d_params, d_tc, n, c->d_gsums, st));
-    else
-        FCAS_CUDA(launch_grad_sums<double>(plan, k1b, c->k_lo, c->k_hi, c->d_params, d_tc, n, c->d_gsums, st,
-                                           c->setup.precision == FCAS_PREC_FF));
-    FCAS_CUDA(launch_grad_final(d_theta, d_tc, n, c->d_gsums, c->d_det, c->d_sigma2s, c->setup.n_det, c->setup.f_low,
-                                c->df, d_grad, st));
+    FCAS_CUDA(gradient_device(c, n, d_theta, d_tc, d_grad, st));
     if (!g_dev) {
         FCAS_CUDA(cudaMemcpyAsync(grad, d_grad, sizeof(double) * 4 * (size_t)n, cudaMemcpyDeviceToHost, st));
     }
     if (!th_dev || !tc_dev || !g_dev) FCAS_CUDA(cudaStreamSynchronize(st));
+    return FCAS_OK;
+}
+
+int fcas_polish(fcas_ctx* c, int64_t n, double* theta, double* fitness, int64_t* tc, int32_t steps,
+                const double* scales, int32_t max_halvings, int32_t* accepted, void* stream) {
+    NvtxRange nvtx_("fcas_polish");
+    g_last_error.clear();
+    if (!c) return fail(FCAS_ERR_INVALID, "fcas_polish: NULL context");
+    if (n < 0 || steps < 0 || max_halvings < 1)
+        return fail(FCAS_ERR_INVALID, "fcas_polish: need n >= 0, steps >= 0 and max_halvings >= 1");
+    if (n == 0) return FCAS_OK;
+    if (int rc0 = check_ctx_device(c, "fcas_polish")) return rc0;
+    if (!theta || !fitness || !tc) return fail(FCAS_ERR_INVALID, "fcas_polish: NULL array");
+    PolishScales sc{{1e-2, 1e-2, 1e-4, 1e-4}};
+    if (scales) {
+        for (int m = 0; m < 4; ++m) {
+            if (!(std::isfinite(scales[m]) && scales[m] > 0.0))
+                return fail(FCAS_ERR_INVALID, "fcas_polish: scales must be finite and > 0");
+            sc.s[m] = scales[m];
+        }
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool th_dev = is_device_ptr(theta), f_dev = is_device_ptr(fitness), t_dev = is_device_ptr(tc);
+    const bool a_dev = accepted && is_device_ptr(accepted);
+    int rc = ensure_particles(c, n);
+    if (!rc) rc = ensure_scratch(c);
+    if (!rc) rc = ensure_grad(c, n);
+    if (rc) return rc;
+    // working arrays: theta, trial points, directions, gradients [n][4]; fitness, trial fitness and step
+    // lengths [n]; tc and trial tc [n]; done and accepted flags [n]; the count of particles still searching
+    const size_t r4 = align256(sizeof(double) * 4 * n), r1 = align256(sizeof(double) * n);
+    const size_t ri = align256(sizeof(int64_t) * n), rf = align256(sizeof(int32_t) * n);
+    const size_t need = 4 * r4 + 3 * r1 + 2 * ri + 2 * rf + 256;
+    if (need > c->polish_bytes) {
+        if (c->d_polish) cudaFree(c->d_polish);
+        c->d_polish = nullptr;
+        c->polish_bytes = 0;
+        rc = dev_alloc(&c->d_polish, need, "polishing buffers");
+        if (rc) return rc;
+        c->polish_bytes = need;
+    }
+    unsigned char* b = c->d_polish;
+    double* w_th = reinterpret_cast<double*>(b);
+    double* w_cand = reinterpret_cast<double*>(b + r4);
+    double* w_dir = reinterpret_cast<double*>(b + 2 * r4);
+    double* w_grad = reinterpret_cast<double*>(b + 3 * r4);
+    double* w_fit = reinterpret_cast<double*>(b + 4 * r4);
+    double* w_cfit = reinterpret_cast<double*>(b + 4 * r4 + r1);
+    double* w_step = reinterpret_cast<double*>(b + 4 * r4 + 2 * r1);
+    int64_t* w_tc = reinterpret_cast<int64_t*>(b + 4 * r4 + 3 * r1);
+    int64_t* w_ctc = reinterpret_cast<int64_t*>(b + 4 * r4 + 3 * r1 + ri);
+    int32_t* w_done = reinterpret_cast<int32_t*>(b + 4 * r4 + 3 * r1 + 2 * ri);
+    int32_t* w_acc = reinterpret_cast<int32_t*>(b + 4 * r4 + 3 * r1 + 2 * ri + rf);
+    int32_t* w_searching = reinterpret_cast<int32_t*>(b + 4 * r4 + 3 * r1 + 2 * ri + 2 * rf);
+
+    FCAS_CUDA(cudaMemcpyAsync(w_th, theta, sizeof(double) * 4 * (size_t)n,
+                              th_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    FCAS_CUDA(cudaMemsetAsync(w_acc, 0, sizeof(int32_t) * (size_t)n, st));
+    // the fitness at the starting points
+    FCAS_CUDA(launch_geometry(w_th, n, c->d_params, c->d_det, c->d_sigma2s, c->setup.n_det, c->setup.f_low, c->df, st));
+    FCAS_CUDA(launch_passes(c, n, w_fit, w_tc, st));
+    for (int32_t step = 0; step < steps; ++step) {
+        FCAS_CUDA(gradient_device(c, n, w_th, w_tc, w_grad, st));
+        FCAS_CUDA(launch_polish_direction(w_th, w_grad, sc, n, w_dir, w_step, w_done, st));
+        for (int32_t h = 0; h < max_halvings; ++h) {
+            FCAS_CUDA(cudaMemsetAsync(w_searching, 0, sizeof(int32_t), st));
+            FCAS_CUDA(launch_polish_candidate(w_th, w_dir, w_step, w_done, n, w_cand, st));
+            FCAS_CUDA(launch_geometry(w_cand, n, c->d_params, c->d_det, c->d_sigma2s, c->setup.n_det, c->setup.f_low,
+                                      c->df, st));
+            FCAS_CUDA(launch_passes(c, n, w_cfit, w_ctc, st));
+            FCAS_CUDA(launch_polish_accept(w_th, w_fit, w_tc, w_cand, w_cfit, w_ctc, w_step, w_done, w_acc, n,
+                                           w_searching, st));
+            int32_t searching = 0;
+            FCAS_CUDA(cudaMemcpyAsync(&searching, w_searching, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+            FCAS_CUDA(cudaStreamSynchronize(st));
+            if (searching == 0) break;
+        }
+    }
+    FCAS_CUDA(cudaMemcpyAsync(theta, w_th, sizeof(double) * 4 * (size_t)n,
+                              th_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    FCAS_CUDA(cudaMemcpyAsync(fitness, w_fit, sizeof(double) * (size_t)n,
+                              f_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    FCAS_CUDA(cudaMemcpyAsync(tc, w_tc, sizeof(int64_t) * (size_t)n,
+                              t_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    if (accepted)
+        FCAS_CUDA(cudaMemcpyAsync(accepted, w_acc, sizeof(int32_t) * (size_t)n,
+                                  a_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    FCAS_CUDA(cudaStreamSynchronize(st));
+    if (const unsigned int bad = take_index_checks(st) | take_index_checks_ff(st))
+        return fail(FCAS_ERR_CUDA, "fcas_polish: index checks failed (bits 0x%x)", bad);
     return FCAS_OK;
 }
 
@@ -999,6 +1147,7 @@ int fcas_condition_number(fcas_ctx* c, int64_t n, const double* theta, double* k
     if (!c) return fail(FCAS_ERR_INVALID, "fcas_condition_number: NULL context");
     if (n < 0) return fail(FCAS_ERR_INVALID, "fcas_condition_number: n < 0");
     if (n == 0) return FCAS_OK;
+    if (int rc0 = check_ctx_device(c, "fcas_condition_number")) return rc0;
     if (!theta || !kappa) return fail(FCAS_ERR_INVALID, "fcas_condition_number: NULL array");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const bool th_dev = is_device_ptr(theta), k_dev = is_device_ptr(kappa);

@@ -134,6 +134,32 @@ cudaError_t launch_check_psd(const double* psd, int n_det, int64_t row, int64_t 
     return cudaGetLastError();
 }
 
+// One-sided noise PSD of every detector from the analytic fit to the aLIGO design sensitivity
+// (Sec. II.A noise model; the paper's own curves are not tabulated):
+//   S(f) = 1e-49 [x^-4.14 - 5 x^-2 + 111 (1 - x^2 + x^4/2) / (1 + x^2/2)],  x = f / 215 Hz,
+// on the band bins f_k = k df, k_lo <= k <= k_hi, of rows of length `row`; the other bins are set
+// to zero (they are never read).
+__global__ void analytic_psd_kernel(double* __restrict__ psd, int n_det, int64_t row, int64_t k_lo, int64_t k_hi,
+                                    double df) {
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < row * n_det;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = g % row;
+        double v = 0.0;
+        if (k >= k_lo && k <= k_hi) {
+            const double x = (double)k * df / 215.0;
+            const double x2 = x * x;
+            v = 1e-49 * (pow(x, -4.14) - 5.0 / x2 + 111.0 * (1.0 - x2 + 0.5 * x2 * x2) / (1.0 + 0.5 * x2));
+        }
+        psd[g] = v;
+    }
+}
+
+cudaError_t launch_analytic_psd(double* psd, int n_det, int64_t row, int64_t k_lo, int64_t k_hi, double df,
+                                cudaStream_t s) {
+    analytic_psd_kernel<<<1024, 256, 0, s>>>(psd, n_det, row, k_lo, k_hi, df);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------------------------------
 // <h_c|h_c>^i = 4 df sum_{k in band} f_k^{-7/3} / S^i[k] (Sec. II.D), fixed-order two-level reduction
 // ------------------------------------------------------------------------------------------

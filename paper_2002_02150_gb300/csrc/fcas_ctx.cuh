@@ -25,6 +25,7 @@ inline size_t inter_bytes_per_particle(int precision, int64_t n_fft) {
 
 struct fcas_ctx {
     fcas_setup setup{};
+    int device = -1;                // CUDA device current at create: every array of the context lives there
     int log_n = 0, log_n1 = 0, log_n2 = 0;
     int64_t n1 = 0, n2 = 0;
     int64_t k_lo = 0, k_hi = 0;
@@ -73,6 +74,8 @@ struct fcas_ctx {
     double* d_gsums = nullptr;       // [n][D][12] per-detector sums at t*
     double* d_gstage = nullptr;      // [n][4] gradient staging for host outputs
     int64_t grad_cap = 0;
+    unsigned char* d_polish = nullptr;  // working arrays of fcas_polish
+    size_t polish_bytes = 0;
     // particle swarm search
     unsigned char* d_pso = nullptr;  // state, parameters, fitness, counters and results of the swarm
     size_t pso_bytes = 0;
@@ -84,6 +87,13 @@ struct fcas_ctx {
 };
 
 namespace fcas {
+
+// FCAS_OK when the device current on the calling thread is the one the context was created on;
+// otherwise FCAS_ERR_INVALID (or FCAS_ERR_CUDA) with a message naming `fn` and both devices.
+int check_ctx_device(const fcas_ctx* c, const char* fn);
+// FCAS_OK when p is memory the current device can use as device memory (device or managed
+// allocation of that device); FCAS_ERR_INVALID with a message naming `fn` and `what` otherwise.
+int check_device_array(const void* p, const char* fn, const char* what);
 
 // Pointers and sizes the fitness kernels need, taken from a prepared context.
 // Pass A / pass B of one chunk in the context's form.

@@ -22,10 +22,26 @@
 
 #include "fcas_internal.cuh"
 #include "fcas_ff.cuh"
+#include "fcas_x2.cuh"
 
 namespace fcas {
 
 template <> struct cplx_of<ffloat> { using type = ff2; };
+
+// Element type of the per-stage twiddle tables of a transform over cplx<Real> values: the value type
+// itself, except for the packed two-series form, whose lanes share one scalar twiddle.
+template <typename Real> struct fft_tw_of { using type = cplx<Real>; };
+template <> struct fft_tw_of<x2f> { using type = float2; };
+template <typename Real> using fft_tw = typename fft_tw_of<Real>::type;
+__device__ __forceinline__ float2 tw_one(float2) { return make_float2(1.0f, 0.0f); }
+__device__ __forceinline__ double2 tw_one(double2) { return make_double2(1.0, 0.0); }
+__device__ __forceinline__ ff2 tw_one(ff2) { return ff2{ffloat(1.0f, 0.0f), ffloat(0.0f, 0.0f)}; }
+
+// a + S i b and a - S i b (S = +1 or -1), the multiplication by +-i folded into the addition
+template <int S, typename C> __device__ __forceinline__ C add_si(C a, C b) {
+    return S > 0 ? mkc(a.x - b.y, a.y + b.x) : mkc(a.x + b.y, a.y - b.x);
+}
+template <int S, typename C> __device__ __forceinline__ C sub_si(C a, C b) { return add_si<-S>(a, b); }
 
 // read-only cached load of a complex table entry
 __device__ __forceinline__ float2 ldg_c(const float2* p) { return __ldg(p); }
@@ -69,11 +85,21 @@ enum IndexCheck { kCheckExchangeRead = 0, kCheckExchangeWrite = 1, kCheckTwiddle
 template <int S, typename C>
 __device__ __forceinline__ void r16_dft4(C& a0, C& a1, C& a2, C& a3) {
     C t0 = a0 + a2, t1 = a0 - a2, t2 = a1 + a3, t3 = a1 - a3;
-    C it3 = mul_si<S>(t3);
     a0 = t0 + t2;
     a2 = t0 - t2;
-    a1 = t1 + it3;
-    a3 = t1 - it3;
+    a1 = add_si<S>(t1, t3);
+    a3 = sub_si<S>(t1, t3);
+}
+
+// the same transform with a2 given before its multiplication by S i (a twiddle of a quarter turn
+// folded into the additions)
+template <int S, typename C>
+__device__ __forceinline__ void r16_dft4_a2si(C& a0, C& a1, C& a2, C& a3) {
+    C t0 = add_si<S>(a0, a2), t1 = sub_si<S>(a0, a2), t2 = a1 + a3, t3 = a1 - a3;
+    a0 = t0 + t2;
+    a2 = t0 - t2;
+    a1 = add_si<S>(t1, t3);
+    a3 = sub_si<S>(t1, t3);
 }
 
 // the same transform when a2 = a3 = 0 (the first layer of a column whose upper half is zero):
@@ -81,11 +107,10 @@ __device__ __forceinline__ void r16_dft4(C& a0, C& a1, C& a2, C& a3) {
 template <int S, typename C>
 __device__ __forceinline__ void r16_dft4_lowhalf(C& a0, C& a1, C& a2, C& a3) {
     const C x0 = a0, x1 = a1;
-    const C ix1 = mul_si<S>(x1);
     a0 = x0 + x1;
     a2 = x0 - x1;
-    a1 = x0 + ix1;
-    a3 = x0 - ix1;
+    a1 = add_si<S>(x0, x1);
+    a3 = sub_si<S>(x0, x1);
 }
 
 // x * e^{S 2 pi i M / 16}
@@ -93,7 +118,9 @@ template <int S, int M, typename C>
 __device__ __forceinline__ C rot16(C x) {
     using R = decltype(x.x);
     constexpr int m = M & 15;
-    if constexpr (m == 0) {
+    if constexpr (std::is_same<C, c32x2>::value) {
+        return rot16_x2<S, m>(x);
+    } else if constexpr (m == 0) {
         return x;
     } else if constexpr (m == 4) {
         return mul_si<S>(x);
@@ -137,14 +164,13 @@ __device__ __forceinline__ void dft8(C (&a)[8]) {
         r16_dft4<S>(o0, o1, o2, o3);
     }
     o1 = rot16<S, 2>(o1);
-    o2 = rot16<S, 4>(o2);
     o3 = rot16<S, 6>(o3);
     a[0] = e0 + o0;
     a[4] = e0 - o0;
     a[1] = e1 + o1;
     a[5] = e1 - o1;
-    a[2] = e2 + o2;
-    a[6] = e2 - o2;
+    a[2] = add_si<S>(e2, o2);   // o2 e^{S 2 pi i 2 / 8} = S i o2
+    a[6] = sub_si<S>(e2, o2);
     a[3] = e3 + o3;
     a[7] = e3 - o3;
 }
@@ -172,7 +198,7 @@ __device__ __forceinline__ void dft16(C (&a)[16]) {
     y1[2] = rot16<S, 2>(y1[2]);
     y1[3] = rot16<S, 3>(y1[3]);
     y2[1] = rot16<S, 2>(y2[1]);
-    y2[2] = rot16<S, 4>(y2[2]);
+    // y2[2] e^{S 2 pi i 4 / 16} = S i y2[2]: folded into its second-layer transform below
     y2[3] = rot16<S, 6>(y2[3]);
     y3[1] = rot16<S, 3>(y3[1]);
     y3[2] = rot16<S, 6>(y3[2]);
@@ -180,7 +206,8 @@ __device__ __forceinline__ void dft16(C (&a)[16]) {
 #pragma unroll
     for (int k1 = 0; k1 < 4; ++k1) {
         C b0 = y0[k1], b1 = y1[k1], b2 = y2[k1], b3 = y3[k1];
-        r16_dft4<S>(b0, b1, b2, b3);
+        if (k1 == 2) r16_dft4_a2si<S>(b0, b1, b2, b3);
+        else r16_dft4<S>(b0, b1, b2, b3);
         a[k1] = b0;
         a[k1 + 4] = b1;
         a[k1 + 8] = b2;
@@ -205,8 +232,9 @@ __device__ __forceinline__ void dft_r(C (&a)[R]) {
 // loaded and the other powers formed by products); fewer instructions, a few more registers.
 template <typename Real, int S, int LOG_L, int DONE, int MAXRB, bool PP, bool LH = false, bool TWL = false, int PS = 4>
 __device__ __forceinline__ void fftr_stage(cplx<Real> (&v)[fftr_v(LOG_L, MAXRB)], cplx<Real>* buf0, int es, int j,
-                                           const cplx<Real>* __restrict__ stw, int alt, int par0) {
+                                           const fft_tw<Real>* __restrict__ stw, int alt, int par0) {
     using C = cplx<Real>;
+    using W = fft_tw<Real>;
     constexpr int L = 1 << LOG_L;
     constexpr int V = fftr_v(LOG_L, MAXRB);
     constexpr int G = L / V;
@@ -243,10 +271,10 @@ __device__ __forceinline__ void fftr_stage(cplx<Real> (&v)[fftr_v(LOG_L, MAXRB)]
         for (int r = 0; r < R; ++r) a[r] = v[h + r * T];
         if constexpr (NS > 1) {
             const int jm = jj & (NS - 1);
-            const C* t = stw + (NS - 1) + jm;
+            const W* t = stw + (NS - 1) + jm;
             if constexpr (R >= 8 && TWL && !std::is_same<Real, ffloat>::value) {
-                C wl[4], wh[R / 4];
-                wl[0] = wh[0] = mkc((Real)1, (Real)0);
+                W wl[4], wh[R / 4];
+                wl[0] = wh[0] = tw_one(W{});
 #pragma unroll
                 for (int r = 1; r < 4; ++r) {
                     wl[r] = wl[0];
@@ -272,7 +300,7 @@ __device__ __forceinline__ void fftr_stage(cplx<Real> (&v)[fftr_v(LOG_L, MAXRB)]
                 // w^r for r = 1..R-1 from two table entries: w and w^4 (powers by products, <= 3 roundings);
                 // the float-float form loads every power instead (a double-word product costs more
                 // than a load)
-                C w1 = mkc((Real)1, (Real)0), w4 = w1;
+                W w1 = tw_one(W{}), w4 = w1;
                 if (FCAS_CHECK((NS - 1) + jm + 3 * NS < L, kCheckTwiddle)) {
                     w1 = ldg_c(t);
                     w4 = ldg_c(t + 3 * NS);
@@ -281,12 +309,12 @@ __device__ __forceinline__ void fftr_stage(cplx<Real> (&v)[fftr_v(LOG_L, MAXRB)]
                     w1 = cconj(w1);
                     w4 = cconj(w4);
                 }
-                const C w2 = cmul(w1, w1);
-                const C w3 = cmul(w2, w1);
+                const W w2 = cmul(w1, w1);
+                const W w3 = cmul(w2, w1);
                 a[1] = cmul(a[1], w1);
                 a[2] = cmul(a[2], w2);
                 a[3] = cmul(a[3], w3);
-                C wb = w4;
+                W wb = w4;
 #pragma unroll
                 for (int hi = 1; hi < R / 4; ++hi) {
                     a[4 * hi] = cmul(a[4 * hi], wb);
@@ -298,7 +326,7 @@ __device__ __forceinline__ void fftr_stage(cplx<Real> (&v)[fftr_v(LOG_L, MAXRB)]
             } else {
 #pragma unroll
                 for (int r = 1; r < R; ++r) {
-                    C w = mkc((Real)1, (Real)0);
+                    W w = tw_one(W{});
                     if (FCAS_CHECK((NS - 1) + (r - 1) * NS + jm < L, kCheckTwiddle)) w = ldg_c(t + (r - 1) * NS);
                     if constexpr (S < 0) w = cconj(w);
                     a[r] = cmul(a[r], w);
@@ -344,7 +372,7 @@ __device__ __forceinline__ void fftr_stage(cplx<Real> (&v)[fftr_v(LOG_L, MAXRB)]
 template <typename Real, int S, int LOG_L, int MAXRB, bool PP = false, int DONE = 0, bool LH = false, bool TWL = false,
           int PS = 4>
 __device__ __forceinline__ void fftr(cplx<Real> (&v)[fftr_v(LOG_L, MAXRB)], cplx<Real>* buf, int es, int j,
-                                     const cplx<Real>* __restrict__ stw, int alt = 0, int par0 = 0) {
+                                     const fft_tw<Real>* __restrict__ stw, int alt = 0, int par0 = 0) {
     if constexpr (DONE < LOG_L) {
         fftr_stage<Real, S, LOG_L, DONE, MAXRB, PP, LH, TWL, PS>(v, buf, es, j, stw, alt, par0);
         fftr<Real, S, LOG_L, MAXRB, PP, DONE + fftr_radix_bits(LOG_L, DONE, MAXRB), false, TWL, PS>(v, buf, es, j, stw,
@@ -354,7 +382,7 @@ __device__ __forceinline__ void fftr(cplx<Real> (&v)[fftr_v(LOG_L, MAXRB)], cplx
 
 template <typename Real, int S, int LOG_L, bool PP = false>
 __device__ __forceinline__ void fft16(cplx<Real> (&v)[fft16_v(LOG_L)], cplx<Real>* buf, int es, int j,
-                                      const cplx<Real>* __restrict__ stw, int alt = 0, int par0 = 0) {
+                                      const fft_tw<Real>* __restrict__ stw, int alt = 0, int par0 = 0) {
     fftr<Real, S, LOG_L, 4, PP>(v, buf, es, j, stw, alt, par0);
 }
 

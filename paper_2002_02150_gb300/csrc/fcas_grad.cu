@@ -17,14 +17,6 @@ namespace fcas {
 
 constexpr int kGradSums = 12;   // Z, F (= sum k Q), S_53, S_1, S_23, S_13: complex, as (re, im) doubles
 
-__device__ __forceinline__ float frac_mul_ff_g(float ah, float al, float bh, float bl) {
-    const float p = __fmul_rn(ah, bh);
-    float e = __fmaf_rn(ah, bh, -p);
-    e = __fmaf_rn(ah, bl, e);
-    e = __fmaf_rn(al, bh, e);
-    return __fadd_rn(__fsub_rn(p, rintf(p)), e);
-}
-
 template <typename Real>
 __global__ void __launch_bounds__(256)
 grad_sums_kernel(const cplx<Real>* __restrict__ y, bool y_ff, const Basis<Real>* __restrict__ basis,
@@ -61,11 +53,11 @@ grad_sums_kernel(const cplx<Real>* __restrict__ y, bool y_ff, const Basis<Real>*
             double qr, qi, b53, b1, b23, b13;
             if constexpr (sizeof(Real) == 4) {
                 const ChirpPowers cpw = chirp_powers(b);
-                float s = frac_mul_ff_g(pp.ch[0], pp.cl[0], cpw.b53.x, cpw.b53.y);
-                s += frac_mul_ff_g(pp.ch[1], pp.cl[1], cpw.b1.x, cpw.b1.y);
-                s += frac_mul_ff_g(pp.ch[2], pp.cl[2], cpw.b23.x, cpw.b23.y);
-                s += frac_mul_ff_g(pp.ch[3], pp.cl[3], cpw.b13.x, cpw.b13.y);
-                float th = s + frac_mul_ff_g((float)k, 0.0f, pp.dh[i], pp.dl[i]) + (float)shift;
+                float s = frac_mul_ff(pp.ch[0], pp.cl[0], cpw.b53.x, cpw.b53.y);
+                s += frac_mul_ff(pp.ch[1], pp.cl[1], cpw.b1.x, cpw.b1.y);
+                s += frac_mul_ff(pp.ch[2], pp.cl[2], cpw.b23.x, cpw.b23.y);
+                s += frac_mul_ff(pp.ch[3], pp.cl[3], cpw.b13.x, cpw.b13.y);
+                float th = s + frac_mul_ff((float)k, 0.0f, pp.dh[i], pp.dl[i]) + (float)shift;
                 th -= rintf(th);
                 float sn, cs;
                 sincospif(2.0f * th, &sn, &cs);
@@ -271,6 +263,90 @@ cudaError_t launch_grad_final(const double* theta, const int64_t* tc, int64_t n,
                               cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     grad_final_kernel<<<(unsigned)((n + 63) / 64), 64, 0, s>>>(theta, tc, n, sums, det9, s2, n_det, f_star, df, grad);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------
+// Gradient polishing: ascent steps along the adjoint gradient, each halved until the fitness
+// increases (the differentiation form's use of the adjoint; the paper itself only runs the swarm).
+// Per particle, with s = scales (1, 1, tau0, tau1.5) (absolute for the angles, relative for the
+// chirp times): direction d = s^2 g / |s g| (a step of length |s| in the metric of s, uphill),
+// first trial step length 1, halved after every trial that does not raise the fitness.
+// ------------------------------------------------------------------------------------------
+__global__ void polish_direction_kernel(const double* __restrict__ theta, const double* __restrict__ grad,
+                                        PolishScales sc, int64_t n, double* __restrict__ dir,
+                                        double* __restrict__ step, int32_t* __restrict__ done) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    double sg[4], norm2 = 0.0;
+    bool finite = true;
+    for (int m = 0; m < 4; ++m) {
+        const double s = sc.s[m] * (m < 2 ? 1.0 : theta[4 * p + m]);
+        const double g = grad[4 * p + m];
+        finite = finite && isfinite(g) && isfinite(s);
+        sg[m] = s * g;
+        dir[4 * p + m] = s * s * g;
+        norm2 += sg[m] * sg[m];
+    }
+    const double norm = sqrt(norm2);
+    const bool ok = finite && norm > 0.0;
+    for (int m = 0; m < 4; ++m) dir[4 * p + m] = ok ? dir[4 * p + m] / norm : 0.0;
+    step[p] = 1.0;
+    done[p] = ok ? 0 : 1;
+}
+
+// the trial point of every particle still searching; NaN (not evaluated) for the others
+__global__ void polish_candidate_kernel(const double* __restrict__ theta, const double* __restrict__ dir,
+                                        const double* __restrict__ step, const int32_t* __restrict__ done, int64_t n,
+                                        double* __restrict__ cand) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    for (int m = 0; m < 4; ++m)
+        cand[4 * p + m] = done[p] ? __longlong_as_double(0x7ff8000000000000LL)
+                                  : theta[4 * p + m] + step[p] * dir[4 * p + m];
+}
+
+// accept a trial that raises the fitness (a NaN trial never does); otherwise halve the step and count
+// the particle as still searching
+__global__ void polish_accept_kernel(double* __restrict__ theta, double* __restrict__ fit, int64_t* __restrict__ tc,
+                                     const double* __restrict__ cand, const double* __restrict__ cfit,
+                                     const int64_t* __restrict__ ctc, double* __restrict__ step,
+                                     int32_t* __restrict__ done, int32_t* __restrict__ accepted, int64_t n,
+                                     int32_t* __restrict__ searching) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n || done[p]) return;
+    if (cfit[p] > fit[p]) {
+        for (int m = 0; m < 4; ++m) theta[4 * p + m] = cand[4 * p + m];
+        fit[p] = cfit[p];
+        tc[p] = ctc[p];
+        accepted[p] += 1;
+        done[p] = 1;
+    } else {
+        step[p] *= 0.5;
+        atomicAdd(searching, 1);
+    }
+}
+
+cudaError_t launch_polish_direction(const double* theta, const double* grad, const PolishScales& sc, int64_t n,
+                                    double* dir, double* step, int32_t* done, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    polish_direction_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(theta, grad, sc, n, dir, step, done);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_polish_candidate(const double* theta, const double* dir, const double* step, const int32_t* done,
+                                    int64_t n, double* cand, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    polish_candidate_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(theta, dir, step, done, n, cand);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_polish_accept(double* theta, double* fit, int64_t* tc, const double* cand, const double* cfit,
+                                 const int64_t* ctc, double* step, int32_t* done, int32_t* accepted, int64_t n,
+                                 int32_t* searching, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    polish_accept_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(theta, fit, tc, cand, cfit, ctc, step, done,
+                                                                     accepted, n, searching);
     return cudaGetLastError();
 }
 

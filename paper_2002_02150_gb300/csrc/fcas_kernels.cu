@@ -173,9 +173,9 @@ int pass_a_k1b_for(int log_n2, int precision) {
 }
 
 int pass_b_blocks_per_particle(int log_n1, int log_n2, int precision) {
-    const int rb = precision == FCAS_PREC_FP32 ? 4 : 8;
+    const bool fp32 = precision == FCAS_PREC_FP32;
     switch (log_n1) {
-#define FCAS_CASE(LG) case LG: return (1 << log_n2) / pass_b_tb(LG, rb);
+#define FCAS_CASE(LG) case LG: return (1 << log_n2) / (fp32 ? x2_b_tb(LG) : pass_b_tb(LG, 8));
         FCAS_LOG_CASES(FCAS_CASE)
 #undef FCAS_CASE
         default: return -1;
@@ -183,8 +183,8 @@ int pass_b_blocks_per_particle(int log_n1, int log_n2, int precision) {
 }
 
 bool pass_a_radix8_available(int log_n2, int precision, int k1b) {
-    return log_n2 >= 10 && log_n2 <= 12 &&
-           ((precision == FCAS_PREC_FP32 && k1b == 4) || (precision == FCAS_PREC_FF && k1b == 2));
+    if (precision == FCAS_PREC_FP32) return log_n2 >= 10 && ((log_n2 <= 11 && k1b == 4) || (log_n2 <= 12 && k1b == 2));
+    return log_n2 >= 10 && log_n2 <= 12 && precision == FCAS_PREC_FF && k1b == 2;
 }
 
 int pass_a_default_radix_bits(int log_n2, int precision) {
@@ -201,8 +201,9 @@ int pass_a_k1b_variants(int log_n2, int precision, int* out) {
         const int kd = pass_a_k1b(LG, rb);                                                  \
         out[n++] = kd;                                                                      \
         if (rb == 4 && LG >= 8) {                                                           \
-            if (k1b_variant_ok<LG, 4>(kd / 2)) out[n++] = kd / 2;                           \
-            if (k1b_variant_ok<LG, 4>(kd * 2)) out[n++] = kd * 2;                           \
+            if (x2_k1b_ok<LG>(kd / 2)) out[n++] = kd / 2;                                   \
+            if (x2_k1b_ok<LG>(kd * 2)) out[n++] = kd * 2;                                   \
+            if (LG >= 10 && kd / 2 > 1) out[n++] = 1;                                       \
         }                                                                                   \
         return n;                                                                           \
     }

@@ -57,6 +57,15 @@ __device__ __forceinline__ float2 ff_mul_raw(float ah, float al, float bh, float
     e = __fmaf_rn(al, bh, e);
     return make_float2(p, e);
 }
+// frac((ah + al)(bh + bl)) with the leading product split exactly: the result is the product
+// reduced by an integer, accurate to a few float ulps of 1 turn (the FP32 form's phase fractions).
+__device__ __forceinline__ float frac_mul_ff(float ah, float al, float bh, float bl) {
+    const float p = __fmul_rn(ah, bh);
+    float e = __fmaf_rn(ah, bh, -p);
+    e = __fmaf_rn(ah, bl, e);
+    e = __fmaf_rn(al, bh, e);
+    return __fadd_rn(__fsub_rn(p, rintf(p)), e);
+}
 __device__ __forceinline__ ChirpPowers chirp_powers_lean(const BasisF& t) {
     ChirpPowers r;
     r.b13 = make_float2(t.h, t.l);
@@ -123,7 +132,7 @@ cudaError_t launch_split_ff(const double2* src, void* dst, int64_t n, cudaStream
 cudaError_t launch_phase_table_ff(void* dst, int n, cudaStream_t s);
 unsigned int take_index_checks_ff(cudaStream_t s);   // the float-float passes' translation unit
 int pass_a_k1b_for(int log_n2, int precision);
-// compiled pass-A column-block widths for a length: writes up to 3 values, returns the count
+// compiled pass-A column-block widths (radix-16 stages) for a length: writes up to 4 values, returns the count
 int pass_a_k1b_variants(int log_n2, int precision, int* out);
 cudaError_t launch_stage_tables(int log_l, int maxrb, double2* t64, float2* t32, cudaStream_t s);
 // pass A with radix-8 stages (8 values per thread) is compiled for these shapes
@@ -139,6 +148,18 @@ cudaError_t launch_grad_final(const double* theta, const int64_t* tc, int64_t n,
                               const double* det9, const double* s2, int n_det, double f_star, double df, double* grad,
                               cudaStream_t s);
 
+// ---- gradient polishing (fcas_grad.cu) ----
+struct PolishScales {
+    double s[4];   // step scales: absolute for alpha, delta; relative (times tau0, tau1.5) for the chirp times
+};
+cudaError_t launch_polish_direction(const double* theta, const double* grad, const PolishScales& sc, int64_t n,
+                                    double* dir, double* step, int32_t* done, cudaStream_t s);
+cudaError_t launch_polish_candidate(const double* theta, const double* dir, const double* step, const int32_t* done,
+                                    int64_t n, double* cand, cudaStream_t s);
+cudaError_t launch_polish_accept(double* theta, double* fit, int64_t* tc, const double* cand, const double* cfit,
+                                 const int64_t* ctc, double* step, int32_t* done, int32_t* accepted, int64_t n,
+                                 int32_t* searching, cudaStream_t s);
+
 // ---- create path (fcas_create.cu) ----
 cudaError_t launch_tables(int log_n, int log_n1, int log_n2, double2* tw64, double2* twlo64, double2* twhi64,
                           float2* tw32, float2* twlo32, float2* twhi32, cudaStream_t s);
@@ -149,6 +170,9 @@ struct DetShifts {
 cudaError_t launch_time_shift(const double* x, double* y, int n_det, int64_t n, const DetShifts& sh, cudaStream_t s);
 cudaError_t launch_check_psd(const double* psd, int n_det, int64_t row, int64_t k_lo, int64_t k_hi, int* flag,
                              cudaStream_t s);
+// the analytic aLIGO fit on the band bins of every detector's row (fcas_create with psd = NULL)
+cudaError_t launch_analytic_psd(double* psd, int n_det, int64_t row, int64_t k_lo, int64_t k_hi, double df,
+                                cudaStream_t s);
 cudaError_t launch_sigma2(const double* psd, int n_det, int64_t row, int64_t k_lo, int64_t k_hi, double df,
                           double* sigma2, double* work, cudaStream_t s);
 cudaError_t launch_data_fft(const double* data, int n_det, int64_t n_samples, int log_n, int log_n1, int log_n2,

@@ -9,7 +9,9 @@
 #include "fcas_ctx.cuh"
 
 namespace {
-constexpr size_t kStaticScratchBytes = size_t(32) << 20;   // 32 MiB, held on every device that loads the library
+// 32 MiB, allocated on a device when this module is loaded there (lazily: at the first call of the
+// entry point on that device) and held until the process exits
+constexpr size_t kStaticScratchBytes = size_t(32) << 20;
 constexpr int kMaxDevices = 64;
 }  // namespace
 
@@ -43,15 +45,6 @@ int scratch_address(void** out) {
     return FCAS_OK;
 }
 
-bool on_device(const void* p) {
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
 size_t round256(size_t v) { return (v + 255) & ~size_t(255); }
 
 }  // namespace
@@ -63,12 +56,14 @@ extern "C" int fcas_fitness_noalloc(const fcas_ctx* c, int64_t n, const double* 
     if (n < 0) return report_error(FCAS_ERR_INVALID, "fcas_fitness_noalloc: n < 0");
     if (n == 0) return FCAS_OK;
     if (!theta || !fitness || !tc) return report_error(FCAS_ERR_INVALID, "fcas_fitness_noalloc: NULL array");
-    if (!on_device(theta) || !on_device(fitness) || !on_device(tc))
-        return report_error(FCAS_ERR_INVALID,
-                            "fcas_fitness_noalloc: theta, fitness and tc must be device pointers (host arrays would "
-                            "need staging memory)");
+    // the context, the arrays, the scratch address and the stream must all belong to the current device
+    int rc = check_ctx_device(c, "fcas_fitness_noalloc");
+    if (rc == FCAS_OK) rc = check_device_array(theta, "fcas_fitness_noalloc", "theta");
+    if (rc == FCAS_OK) rc = check_device_array(fitness, "fcas_fitness_noalloc", "fitness");
+    if (rc == FCAS_OK) rc = check_device_array(tc, "fcas_fitness_noalloc", "tc");
+    if (rc != FCAS_OK) return rc;
     void* base = nullptr;
-    int rc = scratch_address(&base);
+    rc = scratch_address(&base);
     if (rc != FCAS_OK) return rc;
 
     const bool fp32 = c->setup.precision == FCAS_PREC_FP32;
@@ -105,5 +100,12 @@ extern "C" int fcas_fitness_noalloc(const fcas_ctx* c, int64_t n, const double* 
         if (e == cudaSuccess) e = launch_reduce(partials, c->nb_partials, params, 0, np, fitness + p0, tc + p0, st);
     }
     if (e != cudaSuccess) return report_error(FCAS_ERR_CUDA, cudaGetErrorString(e));
+    // checked build (FCAS_CHECKED): wait for the launches and report a failed index check as this
+    // call's failure; other builds return at once
+    if (const unsigned int bad = take_index_checks(st) | take_index_checks_ff(st)) {
+        char msg[96];
+        snprintf(msg, sizeof(msg), "fcas_fitness_noalloc: index checks failed (bits 0x%x)", bad);
+        return report_error(FCAS_ERR_CUDA, msg);
+    }
     return FCAS_OK;
 }

@@ -1,7 +1,8 @@
 """Python binding of libfcas (argument marshalling only; every computation runs in the library).
 
-Functions carry the C names: ``fcas_create``, ``fcas_fitness``, ``fcas_destroy``,
-``fcas_last_error``, ``fcas_get_info``, ``fcas_profile_enable``, ``fcas_profile_read``.
+Functions carry the C names: ``fcas_create``, ``fcas_fitness``, ``fcas_gradient``, ``fcas_polish``,
+``fcas_search``, ``fcas_destroy``, ``fcas_last_error``, ``fcas_get_info``, ``fcas_profile_enable``,
+``fcas_profile_read`` and the others of include/fcas.h.
 Arrays may be numpy arrays (host memory) or torch CUDA tensors (device memory); device arrays make
 the call asynchronous on the given stream (default: torch's current stream).
 """
@@ -128,6 +129,8 @@ def load_library():
     lib.fcas_tau_tiles.restype = i32
     lib.fcas_condition_number.argtypes = [vp, i64, vp, vp, vp]
     lib.fcas_condition_number.restype = i32
+    lib.fcas_polish.argtypes = [vp, i64, vp, vp, vp, ctypes.c_int32, ctypes.POINTER(dp), ctypes.c_int32, vp, vp]
+    lib.fcas_polish.restype = i32
     _lib = lib
     return lib
 
@@ -197,7 +200,8 @@ FCAS_SETUP_LAZY_SCRATCH = 1
 
 def fcas_create(det, psd, data, n_fft, fs, f_low, f_high, precision="fp32", max_batch=0, stream=None, flags=0,
                 shifts=None):
-    """Prepare a data segment. det: (D, 9) ECEF r, x arm, y arm; psd: (D, n_fft/2+1); data: (D, n_samples).
+    """Prepare a data segment. det: (D, 9) ECEF r, x arm, y arm; psd: (D, n_fft/2+1), or None for the
+    library's analytic aLIGO fit; data: (D, n_samples).
     shifts: optional (D,) circular time shifts in samples (fcas_create_time_shifted)."""
     lib = load_library()
     det = np.asarray(det, dtype=np.float64).reshape(-1, 9)
@@ -212,7 +216,7 @@ def fcas_create(det, psd, data, n_fft, fs, f_low, f_high, precision="fp32", max_
             else int(precision))
     setup = fcas_setup(n_det, prec, n_samples, int(n_fft), float(fs), float(f_low), float(f_high), int(max_batch),
                        int(flags))
-    p_psd, k1 = _ptr(psd, np.float64)
+    p_psd, k1 = (ctypes.c_void_p(None), None) if psd is None else _ptr(psd, np.float64)
     p_data, k2 = _ptr(data, np.float64)
     handle = ctypes.c_void_p()
     if shifts is None:
@@ -252,17 +256,45 @@ def fcas_fitness(ctx, theta, fitness=None, tc=None, stream=None):
     return (k2 if not _is_torch(fitness) else fitness), (k3 if not _is_torch(tc) else tc)
 
 
+def array_desc(a):
+    """(is a CUDA tensor, dtype name, contiguous, device index, shape) of an argument."""
+    if _is_torch(a):
+        return (bool(a.is_cuda), str(a.dtype).replace("torch.", ""), bool(a.is_contiguous()),
+                a.device.index if a.is_cuda else None, tuple(a.shape))
+    a = np.asarray(a)
+    return (False, str(a.dtype), bool(a.flags["C_CONTIGUOUS"]), None, tuple(a.shape))
+
+
+def check_noalloc_arrays(theta, fitness, tc, current_device):
+    """The argument checks of fcas_fitness_noalloc that the library cannot make itself (it does not
+    see the arrays' sizes): theta (n, 4) float64, fitness (>= n elements) float64 and tc (>= n) int64,
+    all contiguous and on the CUDA device `current_device` (the context's device, current for the
+    call). Arguments are array_desc tuples. Returns n."""
+    for (cuda, dtype, contiguous, dev, _), name, want in ((theta, "theta", "float64"), (fitness, "fitness", "float64"),
+                                                          (tc, "tc", "int64")):
+        if not (cuda and dtype == want and contiguous):
+            raise TypeError(f"fcas_fitness_noalloc: {name} must be a contiguous CUDA tensor of {want}")
+        if dev != current_device:
+            raise ValueError(f"fcas_fitness_noalloc: {name} is on cuda:{dev} but cuda:{current_device} is current")
+    shape = theta[4]
+    if len(shape) != 2 or shape[1] != 4:
+        raise ValueError(f"fcas_fitness_noalloc: theta must have shape (n, 4), not {shape}")
+    n = int(shape[0])
+    size = lambda d: int(np.prod(d[4], dtype=np.int64))
+    if size(fitness) < n or size(tc) < n:
+        raise ValueError(f"fcas_fitness_noalloc: fitness and tc need {n} elements, have {size(fitness)} and {size(tc)}")
+    return n
+
+
 def fcas_fitness_noalloc(ctx, theta, fitness, tc, stream=None):
-    """Allocation-free evaluation: theta (n, 4), fitness (n,) and tc (n,) must be torch CUDA tensors
-    (float64, float64, int64, contiguous). Scratch comes from the library's fixed static device array."""
-    lib = load_library()
-    for a, dt in ((theta, "torch.float64"), (fitness, "torch.float64"), (tc, "torch.int64")):
-        if not (_is_torch(a) and a.is_cuda and str(a.dtype) == dt and a.is_contiguous()):
-            raise TypeError("fcas_fitness_noalloc needs contiguous CUDA tensors: theta/fitness float64, tc int64")
-    n = int(theta.shape[0])
-    _check(lib.fcas_fitness_noalloc(ctx.handle, n, ctypes.c_void_p(theta.data_ptr()),
-                                    ctypes.c_void_p(fitness.data_ptr()), ctypes.c_void_p(tc.data_ptr()),
-                                    _stream(stream, theta, fitness, tc)))
+    """Allocation-free evaluation: theta (n, 4), fitness (n,) and tc (n,) must be contiguous torch
+    CUDA tensors (float64, float64, int64) on the current device, which must be the context's.
+    Scratch comes from the library's fixed static device array."""
+    import torch
+    n = check_noalloc_arrays(array_desc(theta), array_desc(fitness), array_desc(tc), torch.cuda.current_device())
+    _check(load_library().fcas_fitness_noalloc(ctx.handle, n, ctypes.c_void_p(theta.data_ptr()),
+                                               ctypes.c_void_p(fitness.data_ptr()), ctypes.c_void_p(tc.data_ptr()),
+                                               _stream(stream, theta, fitness, tc)))
     return fitness, tc
 
 
@@ -461,37 +493,26 @@ def coherent_fitness(ctx, theta):
     return _CF.apply(theta, ctx)
 
 
-def polish(ctx, theta, steps=10, scales=(1e-2, 1e-2, 1e-4, 1e-4), evaluate=None, max_halvings=30):
-    """Gradient ascent from theta (n, 4) numpy: each step moves by s^2 g / |s g| (s = scales, relative
-    for the chirp times) and halves the step until the fitness given by `evaluate` increases (default: this
-    library's fitness). Returns (theta, fitness, accepted steps) per particle."""
-    theta = np.array(theta, dtype=np.float64)
-    if evaluate is None:
-        evaluate = lambda th: fcas_fitness(ctx, th)
-    fit, tc = evaluate(theta)
-    fit = np.array(fit, dtype=np.float64)
-    tc = np.array(tc, dtype=np.int64)
-    accepted = np.zeros(len(theta), dtype=np.int64)
-    for _ in range(steps):
-        g = fcas_gradient(ctx, theta, tc)
-        sc = np.array(scales)[None, :] * np.concatenate([np.ones((len(theta), 2)), theta[:, 2:4]], axis=1)
-        direction = sc * sc * g / np.maximum(np.linalg.norm(sc * g, axis=1, keepdims=True), 1e-300)
-        step = np.ones(len(theta))
-        done = ~np.all(np.isfinite(g), axis=1)
-        for _h in range(max_halvings):
-            if np.all(done):
-                break
-            cand = theta + step[:, None] * direction
-            f2, t2 = evaluate(cand)
-            f2 = np.array(f2)
-            ok = (~done) & (f2 > fit)
-            theta[ok] = cand[ok]
-            fit[ok] = f2[ok]
-            tc[ok] = np.array(t2)[ok]
-            accepted[ok] += 1
-            done |= ok
-            step[~done] *= 0.5
-    return theta, fit, accepted
+def fcas_polish(ctx, theta, steps=10, scales=(1e-2, 1e-2, 1e-4, 1e-4), max_halvings=30, stream=None):
+    """Gradient polishing by the library (C: fcas_polish) of points theta (n, 4), numpy or a torch
+    CUDA tensor (updated in place when it is a contiguous float64 CUDA tensor). Returns (theta,
+    fitness, tc, accepted steps), each in theta's memory kind."""
+    n = int(theta.shape[0])
+    if _is_torch(theta) and theta.is_cuda:
+        import torch
+        th = theta if (theta.dtype == torch.float64 and theta.is_contiguous()) else theta.to(torch.float64).contiguous()
+        fit = torch.empty(n, dtype=torch.float64, device=theta.device)
+        tc = torch.empty(n, dtype=torch.int64, device=theta.device)
+        acc = torch.empty(n, dtype=torch.int32, device=theta.device)
+        ptrs = [ctypes.c_void_p(t.data_ptr()) for t in (th, fit, tc, acc)]
+    else:
+        th = np.array(theta, dtype=np.float64).reshape(n, 4)
+        fit, tc, acc = np.empty(n), np.empty(n, dtype=np.int64), np.empty(n, dtype=np.int32)
+        ptrs = [ctypes.c_void_p(a.ctypes.data) for a in (th, fit, tc, acc)]
+    sc = (ctypes.c_double * 4)(*[float(v) for v in scales])
+    _check(load_library().fcas_polish(ctx.handle, n, ptrs[0], ptrs[1], ptrs[2], int(steps), sc, int(max_halvings),
+                                      ptrs[3], _stream(stream, theta)))
+    return th, fit, tc, acc
 
 
 def fcas_autotune(ctx, n_particles=64, cache_path=None, stream=None):

@@ -5,6 +5,8 @@ S(f) = 1e-49 [x^-4.14 - 5 x^-2 + 111 (1 - x^2 + x^4/2) / (1 + x^2/2)], x = f / 2
 fit stands in for them.
 """
 
+import functools
+
 import numpy as np
 
 
@@ -16,8 +18,19 @@ def aligo_fit_psd(f):
     return np.where(f > 0.0, s, np.inf)
 
 
-def psd_on_grid(n_det, n_fft, fs):
-    """PSD sampled at f_k = k fs / n_fft for k = 0..n_fft/2, repeated for every detector: (D, n_fft/2+1)."""
+@functools.lru_cache(maxsize=8)
+def psd_row(n_fft, fs):
+    """The fit sampled at f_k = k fs / n_fft for k = 0..n_fft/2 (read-only, cached per grid)."""
     f = np.arange(n_fft // 2 + 1, dtype=np.float64) * (fs / n_fft)
     s = aligo_fit_psd(f)
-    return np.repeat(s[None, :], n_det, axis=0)
+    s.setflags(write=False)
+    return s
+
+
+@functools.lru_cache(maxsize=8)
+def psd_on_grid(n_det, n_fft, fs):
+    """PSD sampled at f_k = k fs / n_fft for k = 0..n_fft/2, repeated for every detector: (D, n_fft/2+1)
+    (read-only, cached per grid)."""
+    s = np.repeat(psd_row(n_fft, fs)[None, :], n_det, axis=0)
+    s.setflags(write=False)
+    return s

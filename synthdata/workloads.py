@@ -22,7 +22,7 @@ import math
 
 import numpy as np
 
-from .psd import aligo_fit_psd, psd_on_grid
+from .psd import aligo_fit_psd, psd_on_grid, psd_row
 from .sites import detector_geometry
 
 C_LIGHT = 299792458.0
@@ -175,7 +175,7 @@ def noise_spectrum(w, seed, n_det):
     mask = _band_mask(n, w.fs, w.f_low, w.f_high)
     k = np.nonzero(mask)[0]
     t_pad = n / w.fs
-    s = aligo_fit_psd(k * (w.fs / n))
+    s = psd_row(n, w.fs)[k]
     out = np.zeros((n_det, n // 2 + 1), dtype=np.complex128)
     for i in range(n_det):
         g = _rng(seed, 100 + i)

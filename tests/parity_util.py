@@ -42,3 +42,14 @@ def assert_parity(setup, theta, fit, tc, precision, context=""):
             assert 0 <= tc[j] < setup.n_samples, f"{context} particle {j}: tc {tc[j]} out of range"
             tie = abs(curve[tc[j]] - g_ref) / g_ref
             assert tie <= TIE_RTOL, f"{context} particle {j}: tc {tc[j]} vs {t_ref}, not a tie ({tie:.2e})"
+
+
+def assert_parity_pooled(results, fit, tc, precision, context="", probe_index=0):
+    """The parity rule of assert_parity on oracle_pool results: results[j] = (max Gamma^2, lowest
+    argmax, [Gamma^2 at probe lags]) where probe `probe_index` is the GPU's tc of particle j."""
+    for j, (g_ref, t_ref, probe) in enumerate(results):
+        rel = abs(fit[j] - g_ref) / g_ref
+        assert rel <= RTOL[precision], f"{context} particle {j}: Gamma^2 {fit[j]!r} vs {g_ref!r} (rel {rel:.2e})"
+        if tc[j] != t_ref:
+            tie = abs(probe[probe_index] - g_ref) / g_ref
+            assert tie <= TIE_RTOL, f"{context} particle {j}: tc {tc[j]} vs {t_ref}, not a tie ({tie:.2e})"

@@ -86,6 +86,9 @@ def test_create_rejects_invalid_setup(lib, over, needle):
 def test_null_arguments_are_rejected(lib):
     assert lib.fcas_create(None, None, None, None, None, None) == -1
     assert lib.fcas_fitness(None, 1, None, None, None, None) == -1
+    assert lib.fcas_fitness_noalloc(None, 1, None, None, None, None) == -1
+    assert lib.fcas_polish(None, 1, None, None, None, 1, None, 1, None, None) == -1
+    assert lib.fcas_gradient(None, 1, None, None, None, None) == -1
     lib.fcas_destroy(None)
     assert lib.fcas_version() >= 100
 

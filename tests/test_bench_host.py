@@ -57,3 +57,23 @@ def test_reference_arm_prints_one_contract_line():
     assert out["impl"] == "reference" and out["steps"] == 2 and out["warmup"] == 1 and out["value"] > 0
     assert out["cpu_baseline"]["kind"] == "oracle" and out["cpu_baseline"]["value"] == out["value"]
     assert out["e2e"]["h2d_bytes_per_step"] == 0 and out["e2e"]["value"] == out["value"]
+
+
+def test_uneven_segments_cycle_15_30_60_minutes():
+    lengths = [bench._segment_workload(s, (1.4, 1.6, 12.0)) for s in range(6)]
+    assert [w.n_fft for w in lengths] == [1 << 21, 1 << 22, 1 << 23] * 2
+    assert [w.n_samples for w in lengths[:3]] == [15 * 60 * 2048, 30 * 60 * 2048, 60 * 60 * 2048]
+    assert all(w.n_samples <= w.n_fft and w.fs == 2048.0 for w in lengths)
+    assert lengths[0].m1 == 1.4 and lengths[0].m2 == 1.6 and lengths[0].snr == 12.0
+
+
+def test_oracle_judgements_report_fitness_and_argmax():
+    import synthdata as sd
+    from oracle import fcas_oracle as o
+    w = sd.SMALL
+    th = sd.make_particles(w, 2, seed=5)
+    got = bench.oracle_judgements({"pts": (w.name, 5, {}, th.tolist())})
+    data = sd.make_dataset(w, seed=5)
+    setup = o.OracleSetup(data["det"], data["psd"], data["data"], w.n_fft, w.fs, w.f_low, w.f_high)
+    for (v, t), p in zip(got["pts"], th):
+        assert (v, t) == o.fitness(setup, p)

@@ -1,9 +1,9 @@
 """Checked build (FCAS_CHECKED) of the fitness kernels: every shared-memory exchange index, stage
 twiddle index and global spectrum / basis / intermediate index is recomputed from its definition
 and range-tested on the device (the fast padded-address identities included); a failed test is
-recorded instead of performed and makes fcas_fitness return an error. The checked library runs
-in a child process over every test size and compiled launch shape, and its results must equal the
-normal build's exactly."""
+recorded instead of performed and makes fcas_fitness (and fcas_fitness_noalloc) return an error.
+The checked library runs in a child process over every test size and compiled launch shape, and its
+results (of both entry points) must equal the normal build's exactly."""
 
 import dataclasses
 import json
@@ -44,6 +44,14 @@ for name, kw, precision, shapes, npart in cases:
                 fc.fcas_set_shape(ctx, *sh)
             f, t = fc.fcas_fitness(ctx, theta)
             out[f"{name}/{precision}/{sh}"] = [f.tolist(), t.tolist()]
+        if name.startswith("N") and shapes == [None]:
+            # the allocation-free entry point of the checked library on the same particles
+            import torch
+            th = torch.tensor(theta, device="cuda:0")
+            f2 = torch.empty(len(theta), dtype=torch.float64, device="cuda:0")
+            t2 = torch.empty(len(theta), dtype=torch.int64, device="cuda:0")
+            fc.fcas_fitness_noalloc(ctx, th, f2, t2)
+            out[f"{name}/{precision}/noalloc"] = [f2.cpu().tolist(), t2.cpu().tolist()]
 print(json.dumps(out))
 """
 
@@ -73,7 +81,8 @@ def _cases(fc):
     cases.append(["64s", dict(base="C1"), "fp32", _shapes(fc, sd.C1), 4])
     cases.append(["64s", dict(base="C1"), "fp64", [None], 3])
     cases.append(["64s", dict(base="C1"), "ff", [None], 3])
-    cases.append(["60min", dict(base="C2"), "fp32", [None], 2])
+    # the 60-min transform's default shape and its one-column and radix-8 shapes
+    cases.append(["60min", dict(base="C2"), "fp32", [None, [0, 1, 8, 4], [0, 2, 8, 3], [0, 4, 8, 3]], 2])
     cases.append(["60min", dict(base="C2"), "ff", [None, [0, 2, 8, 4]], 1])   # radix-8 default, radix 16
     return cases
 
@@ -93,7 +102,7 @@ def test_checked_build_finds_no_index_error_and_changes_no_result():
                        timeout=1800)
     assert r.returncode == 0, r.stderr[-3000:]
     got = json.loads(r.stdout.strip().splitlines()[-1])
-    n = 0
+    n = n_noalloc = 0
     for name, kw, precision, shapes, npart in cases:
         base = kw.pop("base")
         w = dataclasses.replace(getattr(sd, base), **kw)
@@ -108,4 +117,9 @@ def test_checked_build_finds_no_index_error_and_changes_no_result():
                 cf, ct = got[f"{name}/{precision}/{sh}"]
                 assert np.array_equal(f, np.array(cf)) and np.array_equal(t, np.array(ct)), (name, precision, sh)
                 n += 1
-    assert n >= 15
+                if f"{name}/{precision}/noalloc" in got:
+                    cf, ct = got[f"{name}/{precision}/noalloc"]
+                    assert np.array_equal(f, np.array(cf)) and np.array_equal(t, np.array(ct)), (name, precision,
+                                                                                                 "noalloc")
+                    n_noalloc += 1
+    assert n >= 15 and n_noalloc >= 10

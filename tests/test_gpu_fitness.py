@@ -157,22 +157,33 @@ def test_profiling_counts_launches():
 
 
 def test_config2_full_size_sampled():
-    """The 60-min workload in the launch configuration the benchmark times (320 particles, default
-    chunking): every particle has a finite, non-negative fitness and an in-range tc; sampled
-    particles match the oracle one by one in both forms."""
+    """The 60-min workload in the launch configuration the benchmark times (320 particles in chunks
+    of 64): every particle has a finite, non-negative fitness and an in-range tc; 32 particles spread
+    over every chunk match the oracle one by one in the FP32 and float-float forms, and 8 of them in
+    the binary64 form (the oracle runs on the host cores, one process per particle at a time)."""
+    from oracle_pool import oracle_curves
+    from parity_util import assert_parity_pooled
     w = sd.C2
     data = sd.make_dataset(w, 0)
     theta = sd.make_particles(w, seed=0)
-    sample = [0, 157, 319]
-    setup = oracle_setup(w, data)
+    sample = np.linspace(0, len(theta) - 1, 32).astype(int)
+    sample64 = sample[::4]
+    got = {}
     for precision in FORMS:
         with make_ctx(w, data, precision) as ctx:
-            fit, tc = gpu_fitness(ctx, theta if precision == "fp32" else theta[sample])
+            fit, tc = gpu_fitness(ctx, theta if precision == "fp32" else theta[sample if precision == "ff" else sample64])
         if precision == "fp32":
             assert np.all(np.isfinite(fit)) and np.all(fit >= 0)
             assert np.all((tc >= 0) & (tc < w.n_samples))
             fit, tc = fit[sample], tc[sample]
-        assert_parity(setup, theta[sample], fit, tc, precision, f"C2 {precision}")
+        got[precision] = (fit, tc)
+    del data
+    probes = [[got["fp32"][1][j], got["ff"][1][j]] + ([got["fp64"][1][j // 4]] if j % 4 == 0 else [])
+              for j in range(len(sample))]
+    ref = oracle_curves(w, 0, theta[sample], probes)
+    assert_parity_pooled(ref, *got["fp32"], "fp32", "C2 fp32", probe_index=0)
+    assert_parity_pooled(ref, *got["ff"], "ff", "C2 ff", probe_index=1)
+    assert_parity_pooled(ref[::4], *got["fp64"], "fp64", "C2 fp64", probe_index=2)
 
 
 def test_largest_supported_length_sampled():
@@ -251,3 +262,75 @@ def test_paper_chirp_time_box_at_f_star_10hz(precision):
     with make_ctx(w, data, precision) as ctx:
         fit, tc = gpu_fitness(ctx, theta)
     assert_parity(oracle_setup(w, data), theta, fit, tc, precision, "f*=10Hz")
+
+
+def _split_log_n1(log_n):
+    """log2 of the pass-B length N1 the library uses for a length-2^log_n transform (N = N1 N2 with
+    N2 = 2^max(2, log_n - 13, floor(log_n / 2)))."""
+    return log_n - max(2, log_n - 13, log_n // 2)
+
+
+@pytest.mark.parametrize("precision", FORMS)
+@pytest.mark.parametrize("log_n", [14, 15])
+def test_exact_ties_resolve_to_the_lowest_lag(precision, log_n):
+    """Data with period P = N1 (the create-time transform's first length) has a spectrum that is
+    exactly zero off the multiples of N / P in every step of the library (transforms of constant
+    columns, zeros times twiddles), so Gamma^2(t) repeats exactly with period P and every maximum is
+    tied with its copies P, 2P, ... later. The library must return the lowest of the tied lags, as
+    np.argmax does: tc < P, on the oracle's maximum modulo P (or a tie within 1e-5)."""
+    import paper_2002_02150_gb300 as fc
+    n = 1 << log_n
+    period = 1 << _split_log_n1(log_n)
+    w = dataclasses.replace(sd.SMALL, n_fft=n, n_samples=n, fs=1024.0, f_low=40.0, f_high=200.0)
+    base = sd.make_dataset(w, 81, inject=False)
+    rng = np.random.default_rng(81)
+    data = np.tile(rng.standard_normal((w.n_det, period)) * 1e-21, (1, n // period))
+    theta = sd.make_particles(w, 6, seed=81)
+    with fc.fcas_create(base["det"], base["psd"], data, w.n_fft, w.fs, w.f_low, w.f_high, precision=precision) as ctx:
+        assert fc.fcas_get_info(ctx)["n1"] == period
+        fit, tc = gpu_fitness(ctx, theta)
+    setup = o.OracleSetup(base["det"], base["psd"], data, w.n_fft, w.fs, w.f_low, w.f_high)
+    for j, th in enumerate(theta):
+        curve = o.fitness_curve(setup, th)
+        # the premise: the oracle's curve repeats with period P (to its own rounding)
+        assert np.max(np.abs(curve - np.tile(curve[:period], n // period))) <= 1e-9 * curve.max()
+        g_ref = curve.max()
+        assert abs(fit[j] - g_ref) / g_ref <= RTOL[precision]
+        assert 0 <= tc[j] < period, f"particle {j}: tc {tc[j]} is not the lowest of the tied lags"
+        t_ref = int(np.argmax(curve[:period]))
+        if tc[j] != t_ref:
+            assert abs(curve[tc[j]] - g_ref) / g_ref <= 1e-5, (j, tc[j], t_ref)
+
+
+@pytest.mark.parametrize("precision", FORMS)
+def test_zero_data_ties_every_lag_at_zero(precision):
+    """All-zero data: Gamma^2(t) = 0 for every lag, so the maximum is 0 and the lowest lag is 0."""
+    import paper_2002_02150_gb300 as fc
+    w = sd.SMALL
+    base = sd.make_dataset(w, 82, inject=False)
+    theta = sd.make_particles(w, 5, seed=82)
+    with fc.fcas_create(base["det"], base["psd"], np.zeros((w.n_det, w.n_samples)), w.n_fft, w.fs, w.f_low,
+                        w.f_high, precision=precision) as ctx:
+        fit, tc = gpu_fitness(ctx, theta)
+    np.testing.assert_array_equal(fit, np.zeros(5))
+    np.testing.assert_array_equal(tc, np.zeros(5, dtype=np.int64))
+
+
+@pytest.mark.parametrize("precision", FORMS)
+def test_null_psd_is_the_analytic_aligo_fit(precision):
+    """psd = NULL at create evaluates the analytic aLIGO fit on the device: the context equals one
+    created from the same fit sampled on the host (to the rounding of the two evaluations of the fit)
+    and matches the oracle given the host-sampled fit."""
+    import paper_2002_02150_gb300 as fc
+    w = sd.C1
+    data = sd.make_dataset(w, 83)
+    theta = sd.make_particles(w, 12, seed=83)
+    with fc.fcas_create(data["det"], None, data["data"], w.n_fft, w.fs, w.f_low, w.f_high, precision=precision) as c0, \
+            make_ctx(w, data, precision) as c1:
+        i0, i1 = fc.fcas_get_info(c0), fc.fcas_get_info(c1)
+        np.testing.assert_allclose(i0["sigma2"][:w.n_det], i1["sigma2"][:w.n_det], rtol=1e-13)
+        f0, t0 = gpu_fitness(c0, theta)
+        f1, t1 = gpu_fitness(c1, theta)
+    np.testing.assert_allclose(f0, f1, rtol=1e-6 if precision == "fp32" else 1e-12)
+    np.testing.assert_array_equal(t0, t1)
+    assert_parity(oracle_setup(w, data), theta, f0, t0, precision, "psd=NULL")
