@@ -101,13 +101,6 @@ __host__ __device__ constexpr int pass_b_tb(int log_l, int real_bytes) {
 __host__ __device__ constexpr int pass_b_threads(int log_l, int real_bytes) {
     return pass_b_tb(log_l, real_bytes) * ((1 << log_l) / shape_v(log_l));
 }
-// Pass B of the FP32 form (both series packed in one transform): rows per CTA for a target CTA size
-#ifndef FCAS_X2_B_THREADS
-#define FCAS_X2_B_THREADS 256
-#endif
-__host__ __device__ constexpr int x2_b_tb(int log_l) {
-    return imin_c(imin_c(16, imax_c(1, FCAS_X2_B_THREADS / ((1 << log_l) / shape_v(log_l)))), (1 << log_l) / 2);
-}
 // Transforms per particle between the passes: the two network-weighted series.
 constexpr int kSeries = 2;
 

@@ -175,7 +175,7 @@ int pass_a_k1b_for(int log_n2, int precision) {
 int pass_b_blocks_per_particle(int log_n1, int log_n2, int precision) {
     const bool fp32 = precision == FCAS_PREC_FP32;
     switch (log_n1) {
-#define FCAS_CASE(LG) case LG: return (1 << log_n2) / (fp32 ? x2_b_tb(LG) : pass_b_tb(LG, 8));
+#define FCAS_CASE(LG) case LG: return (1 << log_n2) / pass_b_tb(LG, fp32 ? 4 : 8);
         FCAS_LOG_CASES(FCAS_CASE)
 #undef FCAS_CASE
         default: return -1;

@@ -462,7 +462,7 @@ pass_b_kernel(const cplx<Real>* __restrict__ inter, const ParticleParams* __rest
 // ------------------------------------------------------------------------------------------
 // FP32 form: both network-weighted series in one packed transform (fcas_x2.cuh). Lane 0 of every
 // packed value is P_1 / W_1, lane 1 is P_2 / W_2; the intermediate holds one 16-byte element
-// (re_1, re_2, im_1, im_2) per point: A[p][ta][k1].
+// (re_1, re_2, im_1, im_2) per point, row-major: A[p][ta][k1].
 // ------------------------------------------------------------------------------------------
 __host__ __device__ constexpr int x2_a_threads(int log_l, int k1b, int maxrb = 4) {
     return k1b * ((1 << log_l) / fftr_v(log_l, maxrb));
@@ -477,45 +477,25 @@ __host__ __device__ constexpr int x2_buf_elems(int log_l, int k1b, int maxrb = 4
 __host__ __device__ constexpr bool x2_a_pingpong(int log_l, int k1b, int maxrb = 4) {
     return 2 * sizeof(c32x2) * (size_t)x2_buf_elems(log_l, k1b, maxrb) <= 200 * 1024;
 }
-#ifndef FCAS_X2_CARVEOUT
-#define FCAS_X2_CARVEOUT 0       // 1: ask for the largest shared-memory carveout for the packed passes
-#endif
-#ifndef FCAS_X2_LDG_NA_A
-#define FCAS_X2_LDG_NA_A 0       // 1: pass A's spectrum loads skip L1 allocation (slower: 4.21 -> 4.48 ms)
-#endif
-#ifndef FCAS_X2_LDG_NA_B
-#define FCAS_X2_LDG_NA_B 1       // pass B's intermediate loads (read once) skip L1 allocation
-#endif
-#ifndef FCAS_X2_B_MIN_BLOCKS
-#define FCAS_X2_B_MIN_BLOCKS 2   // resident pass-B CTAs of up to 256 threads the compiler is held to
-#endif
 // resident CTAs the compiler is held to: 512 threads' worth per SM with radix-16 stages (16 values per
 // thread), 1024 threads' worth with radix-8 stages (8 values per thread)
 __host__ __device__ constexpr int x2_min_blocks(int threads, int maxrb = 4) {
-    return imax_c(1, (maxrb == 3 ? 1024 : 512) / threads);
-}
-#ifndef FCAS_X2_TILE
-#define FCAS_X2_TILE 0           // 1: intermediate in 2-row x 4-column tiles (128 bytes); 0: row-major
-#endif
-// Element (ta, k1) of one particle's intermediate (n1 points per row): with FCAS_X2_TILE the rows are
-// stored in pairs and the columns in fours, [ta/2][k1/4][ta%2][k1%4], so that a pass-A CTA of four
-// columns writes whole 128-byte lines (two rows at a time) and a pass-B CTA reads 64-byte pieces;
-// otherwise row-major [ta][k1].
-__device__ __forceinline__ int64_t x2_inter_index(int ta, int k1, int log_n1) {
-#if FCAS_X2_TILE
-    return ((((int64_t)(ta >> 1) << (log_n1 - 2)) + (k1 >> 2)) << 3) + ((ta & 1) << 2) + (k1 & 3);
-#else
-    return ((int64_t)ta << log_n1) + k1;
-#endif
+    return imin_c(16, imax_c(1, (maxrb == 3 ? 1024 : 512) / threads));
 }
 
+// Pass A of the FP32 form as a persistent grid: one wave of resident CTAs, each taking work items
+// (particle, column block) blockIdx.x, blockIdx.x + gridDim.x, ... in the order of the other forms
+// (SUB adjacent column blocks of one particle, then the particles of the chunk, then the next group of
+// column blocks), so that one item's stores drain while the next item loads (60-min pass A 4.27 ->
+// 4.07 ms per 64 particles against one item per CTA). Shapes with two exchange buffers run one item
+// per CTA (the exchange parity restarts with every item).
 template <int LOG_L, int K1B, int MAXRB = 4>
 __global__ void __launch_bounds__(x2_a_threads(LOG_L, K1B, MAXRB),
                                   x2_min_blocks(x2_a_threads(LOG_L, K1B, MAXRB), MAXRB))
 pass_a_x2_kernel(const float2* __restrict__ y, const BasisF* __restrict__ basis,
                  const ParticleParams* __restrict__ params, int64_t p0, int64_t np, int n_det, int log_n1, int sub_req,
                  c32x2* __restrict__ out, const float2* __restrict__ stw, const float2* __restrict__ tw_lo,
-                 const float2* __restrict__ tw_hi) {
+                 const float2* __restrict__ tw_hi, int64_t items) {
     constexpr int L = 1 << LOG_L;
     constexpr int V = fftr_v(LOG_L, MAXRB);
     constexpr int G = L / V;
@@ -523,126 +503,130 @@ pass_a_x2_kernel(const float2* __restrict__ y, const BasisF* __restrict__ basis,
     extern __shared__ __align__(16) unsigned char smem_raw[];
     c32x2* smem = reinterpret_cast<c32x2*>(smem_raw);
     __shared__ DetConst<float> sc;
+    __shared__ float scc[2][4];   // chirp-phase coefficients (hi, lo) of the item's particle
 
     const int c = threadIdx.x % K1B;
     const int j = threadIdx.x / K1B;
-    // CTA order as in the other forms: SUB adjacent column blocks of one particle, then the
-    // particles of the chunk, then the next group of column blocks
     const int nblk = (1 << log_n1) / K1B;
     const int sub = sub_req < nblk ? sub_req : nblk;
-    const int64_t lin = blockIdx.x;
-    const int64_t rest = lin / sub;
-    const int64_t p = rest % np;
-    const int blk = (int)((rest / np) * sub + lin % sub);
-    const int k1 = blk * K1B + c;
-    const ParticleParams* pp = params + p0 + p;
-    if (!pp->valid) return;   // not evaluated (invalid input, or a PSO particle outside its box)
-    if (threadIdx.x < FCAS_MAX_DET) {
-        const int i = threadIdx.x;
-        sc.dh[i] = pp->dh[i];
-        sc.dl[i] = pp->dl[i];
-        sc.w1[i] = pp->w1f[i];
-        sc.w2[i] = pp->w2f[i];
-    }
-    __syncthreads();
     const int n1 = 1 << log_n1;
-
-    // Thread (c, j) owns the bins k = k1 + N1 (j + q G), q < VH: the detector sums per series with
-    // the delay phasors by recurrence, then the chirp phasor (as in the other forms), in scalar FP32.
-    float2 r1[VH], r2[VH];
-#pragma unroll
-    for (int q = 0; q < VH; ++q) r1[q] = r2[q] = make_float2(0.0f, 0.0f);
-    const int64_t bidx0 = ((int64_t)blk * (L / 2) + j) * K1B + c;
-    const BasisF* bb = basis + bidx0;
-    BasisF bq[VH];
-#pragma unroll
-    for (int q = 0; q < VH; ++q)
-        if (FCAS_CHECK(bidx0 + (int64_t)q * G * K1B < ((int64_t)L / 2 << log_n1), kCheckBasis))
-            bq[q] = bb[(int64_t)q * G * K1B];
-    const int kbase = k1 + n1 * j;
-    const int kstep = n1 * G;
-    const int64_t col0 = (int64_t)blk * n_det;
-#pragma unroll
-    for (int i = 0; i < FCAS_MAX_DET; ++i) {
-        if (i >= n_det) break;
-        float fb = frac_mul_ff((float)kbase, 0.0f, sc.dh[i], sc.dl[i]);
-        float fs = frac_mul_ff((float)kstep, 0.0f, sc.dh[i], sc.dl[i]);
-        fb -= rintf(fb);
-        fs -= rintf(fs);
-        float2 dph = fast_phasor(fb);
-        const float2 dstep = fast_phasor(fs);
-        const int64_t yidx0 = ((col0 + i) * (L / 2) + j) * K1B + c;
-        const float2* yd = y + yidx0;
-        const float w1 = sc.w1[i], w2 = sc.w2[i];
-#pragma unroll
-        for (int q = 0; q < VH; ++q) {
-            float2 yv = make_float2(0.0f, 0.0f);
-            if (FCAS_CHECK(yidx0 + (int64_t)q * G * K1B < (int64_t)n_det * ((int64_t)L / 2 << log_n1), kCheckSpectrum)) {
-#if FCAS_X2_LDG_NA_A
-                yv = ld_na(yd + (int64_t)q * G * K1B);
-#else
-                yv = yd[(int64_t)q * G * K1B];
-#endif
+#pragma unroll 1
+    for (int64_t lin = blockIdx.x; lin < items; lin += gridDim.x) {
+        const int64_t rest = lin / sub;
+        const int64_t p = rest % np;
+        const int blk = (int)((rest / np) * sub + lin % sub);
+        const int k1 = blk * K1B + c;
+        const ParticleParams* pp = params + p0 + p;
+        if (!pp->valid) continue;   // not evaluated (invalid input, or a PSO particle outside its box)
+        // the particle's constants in shared memory (earlier items' reads of them all ended before
+        // the barriers of their transforms)
+        if (threadIdx.x < FCAS_MAX_DET) {
+            const int i = threadIdx.x;
+            sc.dh[i] = pp->dh[i];
+            sc.dl[i] = pp->dl[i];
+            sc.w1[i] = pp->w1f[i];
+            sc.w2[i] = pp->w2f[i];
+            if (i < 4) {
+                scc[0][i] = pp->ch[i];
+                scc[1][i] = pp->cl[i];
             }
-            const float2 t = cmul(yv, dph);
-            r1[q].x += w1 * t.x;
-            r1[q].y += w1 * t.y;
-            r2[q].x += w2 * t.x;
-            r2[q].y += w2 * t.y;
-            if (q + 1 < VH) dph = cmul(dph, dstep);
         }
-    }
-    c32x2 v[V];
-    {
-        float cfh[4], cfl[4];
+        __syncthreads();
+
+        // Thread (c, j) owns the bins k = k1 + N1 (j + q G), q < VH: the detector sums per series with
+        // the delay phasors by recurrence, then the chirp phasor (as in the other forms), in scalar FP32.
+        float2 r1[VH], r2[VH];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            cfh[r] = pp->ch[r];
-            cfl[r] = pp->cl[r];
+        for (int q = 0; q < VH; ++q) r1[q] = r2[q] = make_float2(0.0f, 0.0f);
+        // the chirp basis of the thread's bins is requested first: its latency overlaps the detector sums
+        const int64_t bidx0 = ((int64_t)blk * (L / 2) + j) * K1B + c;
+        const BasisF* bb = basis + bidx0;
+        BasisF bq[VH];
+#pragma unroll
+        for (int q = 0; q < VH; ++q)
+            if (FCAS_CHECK(bidx0 + (int64_t)q * G * K1B < ((int64_t)L / 2 << log_n1), kCheckBasis))
+                bq[q] = bb[(int64_t)q * G * K1B];
+        const int kbase = k1 + n1 * j;
+        const int kstep = n1 * G;
+        const int64_t col0 = (int64_t)blk * n_det;
+#pragma unroll
+        for (int i = 0; i < FCAS_MAX_DET; ++i) {
+            if (i >= n_det) break;
+            float fb = frac_mul_ff((float)kbase, 0.0f, sc.dh[i], sc.dl[i]);
+            float fs = frac_mul_ff((float)kstep, 0.0f, sc.dh[i], sc.dl[i]);
+            fb -= rintf(fb);
+            fs -= rintf(fs);
+            float2 dph = fast_phasor(fb);
+            const float2 dstep = fast_phasor(fs);
+            const int64_t yidx0 = ((col0 + i) * (L / 2) + j) * K1B + c;
+            const float2* yd = y + yidx0;
+            const float w1 = sc.w1[i], w2 = sc.w2[i];
+#pragma unroll
+            for (int q = 0; q < VH; ++q) {
+                float2 yv = make_float2(0.0f, 0.0f);
+                if (FCAS_CHECK(yidx0 + (int64_t)q * G * K1B < (int64_t)n_det * ((int64_t)L / 2 << log_n1),
+                               kCheckSpectrum))
+                    yv = yd[(int64_t)q * G * K1B];
+                const float2 t = cmul(yv, dph);
+                r1[q].x += w1 * t.x;
+                r1[q].y += w1 * t.y;
+                r2[q].x += w2 * t.x;
+                r2[q].y += w2 * t.y;
+                if (q + 1 < VH) dph = cmul(dph, dstep);
+            }
+        }
+        c32x2 v[V];
+        {
+            float cfh[4], cfl[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                cfh[r] = scc[0][r];
+                cfl[r] = scc[1][r];
+            }
+#pragma unroll
+            for (int q = 0; q < VH; ++q) {
+                const ChirpPowers b = chirp_powers_lean(bq[q]);
+                float s = frac_mul_ff(cfh[0], cfl[0], b.b53.x, b.b53.y);
+                s += frac_mul_ff(cfh[1], cfl[1], b.b1.x, b.b1.y);
+                s += frac_mul_ff(cfh[2], cfl[2], b.b23.x, b.b23.y);
+                s += frac_mul_ff(cfh[3], cfl[3], b.b13.x, b.b13.y);
+                const float2 cp = fast_phasor(s - rintf(s));
+                v[q] = pack_series(cmul(r1[q], cp), cmul(r2[q], cp));
+            }
         }
 #pragma unroll
-        for (int q = 0; q < VH; ++q) {
-            const ChirpPowers b = chirp_powers_lean(bq[q]);
-            float s = frac_mul_ff(cfh[0], cfl[0], b.b53.x, b.b53.y);
-            s += frac_mul_ff(cfh[1], cfl[1], b.b1.x, b.b1.y);
-            s += frac_mul_ff(cfh[2], cfl[2], b.b23.x, b.b23.y);
-            s += frac_mul_ff(cfh[3], cfl[3], b.b13.x, b.b13.y);
-            const float2 cp = fast_phasor(s - rintf(s));
-            v[q] = pack_series(cmul(r1[q], cp), cmul(r2[q], cp));
+        for (int q = VH; q < V; ++q) v[q] = zero_c32x2();
+        // one transform of both series; stage twiddles w^r (r < 4) and w^{4h} loaded, the rest one
+        // product each (formed once for both series)
+        fftr<x2f, +1, LOG_L, MAXRB, x2_a_pingpong(LOG_L, K1B, MAXRB), 0, true, true, x2_pad_shift(MAXRB)>(
+            v, smem + c, K1B, j, stw, x2_buf_elems(LOG_L, K1B, MAXRB), 0);
+        c32x2* orow = out + ((int64_t)p * L) * n1 + k1;
+        // e^{2 pi i k1 ta / N} for ta = j + q G: the value at q = 0 times powers of the step e^{2 pi i k1 G / N}
+        const int m0 = k1 * j, ms = k1 * G;   // < N
+        float2 w = cmul(__ldg(tw_hi + (m0 >> kTwLoBits)), __ldg(tw_lo + (m0 & ((1 << kTwLoBits) - 1))));
+        const float2 step = cmul(__ldg(tw_hi + (ms >> kTwLoBits)), __ldg(tw_lo + (ms & ((1 << kTwLoBits) - 1))));
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+            const int ta = j + q * G;
+            if (FCAS_CHECK((int64_t)p * L * n1 + k1 + (int64_t)ta * n1 < np * (int64_t)L * n1, kCheckInterWrite))
+                st_stream_x2(orow + (int64_t)ta * n1, cmul(v[q], w));   // streamed: read back only by pass B
+            if (q + 1 < V) w = cmul(w, step);
         }
-    }
-#pragma unroll
-    for (int q = VH; q < V; ++q) v[q] = zero_c32x2();
-    // one transform of both series; stage twiddles w^r (r < 4) and w^{4h} loaded, the rest one
-    // product each (formed once for both series)
-    fftr<x2f, +1, LOG_L, MAXRB, x2_a_pingpong(LOG_L, K1B, MAXRB), 0, true, true, x2_pad_shift(MAXRB)>(
-        v, smem + c, K1B, j, stw, x2_buf_elems(LOG_L, K1B, MAXRB), 0);
-    c32x2* opart = out + ((int64_t)p * L) * n1;
-    // e^{2 pi i k1 ta / N} for ta = j + q G: the value at q = 0 times powers of the step e^{2 pi i k1 G / N}
-    const int m0 = k1 * j, ms = k1 * G;   // < N
-    float2 w = cmul(__ldg(tw_hi + (m0 >> kTwLoBits)), __ldg(tw_lo + (m0 & ((1 << kTwLoBits) - 1))));
-    const float2 step = cmul(__ldg(tw_hi + (ms >> kTwLoBits)), __ldg(tw_lo + (ms & ((1 << kTwLoBits) - 1))));
-#pragma unroll
-    for (int q = 0; q < V; ++q) {
-        const int ta = j + q * G;
-        const int64_t o = x2_inter_index(ta, k1, log_n1);
-        if (FCAS_CHECK(o < (int64_t)L * n1 && (int64_t)p * L * n1 + o < np * (int64_t)L * n1, kCheckInterWrite))
-            st_stream_x2(opart + o, cmul(v[q], w));   // streamed: read back only by pass B
-        if (q + 1 < V) w = cmul(w, step);
     }
 }
 
-__host__ __device__ constexpr int x2_b_threads(int log_l) { return x2_b_tb(log_l) * ((1 << log_l) / shape_v(log_l)); }
+__host__ __device__ constexpr int x2_b_threads(int log_l) { return pass_b_threads(log_l, 4); }
+// resident pass-B CTAs the compiler is held to: two of 256 threads (16 values per thread)
+__host__ __device__ constexpr int x2_b_min_blocks(int log_l) { return x2_b_threads(log_l) > 256 ? 1 : 2; }
 
 template <int LOG_L>
-__global__ void __launch_bounds__(x2_b_threads(LOG_L), x2_b_threads(LOG_L) > 256 ? 1 : FCAS_X2_B_MIN_BLOCKS)
+__global__ void __launch_bounds__(x2_b_threads(LOG_L), x2_b_min_blocks(LOG_L))
 pass_b_x2_kernel(const c32x2* __restrict__ inter, const ParticleParams* __restrict__ params, int64_t p0, int log_n2,
                  int64_t n_samples, const float2* __restrict__ stw, Partial* __restrict__ partials) {
-    // rows are transforms over k1 of length N1 = L
     constexpr int L = 1 << LOG_L;
     constexpr int V = shape_v(LOG_L);
     constexpr int G = L / V;
-    constexpr int TB = x2_b_tb(LOG_L);
+    constexpr int TB = pass_b_tb(LOG_L, 4);
     constexpr int NT = TB * G;
     constexpr int BUF = fft16_buf_elems(LOG_L);
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -657,20 +641,14 @@ pass_b_x2_kernel(const c32x2* __restrict__ inter, const ParticleParams* __restri
     const int ta = blockIdx.x * TB + c;
     const int64_t p = blockIdx.y;
     if (!params[p0 + p].valid) return;   // the final reduce reports NaN for it
-    const c32x2* part = inter + (int64_t)p * n2 * L;
+    const int64_t row0 = ((int64_t)p * n2 + ta) * L;
+    const c32x2* row = inter + row0;
     c32x2 v[V];
 #pragma unroll
     for (int q = 0; q < V; ++q) {
         v[q] = zero_c32x2();
-        const int64_t o = x2_inter_index(ta, j + q * G, LOG_L);
-        if (FCAS_CHECK(o < (int64_t)n2 * L && (int64_t)p * n2 * L + o < (int64_t)gridDim.y * n2 * L,
-                       kCheckInterRead)) {
-#if FCAS_X2_LDG_NA_B
-            v[q] = ld_na(part + o);
-#else
-            v[q] = part[o];
-#endif
-        }
+        if (FCAS_CHECK(row0 + j + q * G < (int64_t)gridDim.y * n2 * L, kCheckInterRead))
+            v[q] = ld_na(row + j + q * G);   // read once: no L1 allocation (60-min pass B 2.13 -> 2.10 ms)
     }
     fft16<x2f, +1, LOG_L>(v, smem + c * BUF, 1, j, stw);
     // Gamma^2(t) = |W_1(t)|^2 + |W_2(t)|^2; t = ta + N2 (j + q G) grows with q, so a strict
@@ -705,15 +683,22 @@ static cudaError_t pass_a_x2_at(const FitnessPlan& pl, const ParticleParams* par
     auto kern = pass_a_x2_kernel<LG, K1B, MAXRB>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-#if FCAS_X2_CARVEOUT
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-    if (e != cudaSuccess) return e;
-#endif
-    const int64_t ctas = np * ((1 << pl.log_n1) / K1B);
+    const int64_t items = np * ((1 << pl.log_n1) / K1B);
+    int64_t ctas = items;
+    if constexpr (!x2_a_pingpong(LG, K1B, MAXRB)) {
+        // one wave: the resident CTAs of every SM
+        int dev = 0, sms = 0, per_sm = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, smem);
+        if (e != cudaSuccess) return e;
+        const int64_t wave = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+        if (wave < ctas) ctas = wave;
+    }
     kern<<<(unsigned)ctas, THREADS, smem, s>>>(static_cast<const float2*>(pl.y), static_cast<const BasisF*>(pl.basis),
                                                params, p0, np, pl.n_det, pl.log_n1, pl.sub, static_cast<c32x2*>(inter),
                                                static_cast<const float2*>(pl.stw_a), static_cast<const float2*>(pl.tw_lo),
-                                               static_cast<const float2*>(pl.tw_hi));
+                                               static_cast<const float2*>(pl.tw_hi), items);
     return cudaGetLastError();
 }
 
@@ -729,10 +714,10 @@ static cudaError_t pass_a_x2_lg(const FitnessPlan& pl, const ParticleParams* par
             if (pl.k1b == 2) return pass_a_x2_at<LG, 2, 3>(pl, params, p0, np, inter, s);
         return cudaErrorInvalidValue;
     }
-    if constexpr (LG >= 10 && KD > 1)
-        if (pl.k1b == 1) return pass_a_x2_at<LG, 1>(pl, params, p0, np, inter, s);   // one column per CTA
     if (pl.radix_bits_a != 4) return cudaErrorInvalidValue;
     if (pl.k1b == KD) return pass_a_x2_at<LG, KD>(pl, params, p0, np, inter, s);
+    if constexpr (LG >= 10 && KD > 1)
+        if (pl.k1b == 1) return pass_a_x2_at<LG, 1>(pl, params, p0, np, inter, s);   // one column per CTA
     if constexpr (LG >= 8) {
         if constexpr (x2_k1b_ok<LG>(KD / 2))
             if (pl.k1b == KD / 2) return pass_a_x2_at<LG, (KD / 2 > 0 ? KD / 2 : 1)>(pl, params, p0, np, inter, s);
@@ -745,15 +730,11 @@ static cudaError_t pass_a_x2_lg(const FitnessPlan& pl, const ParticleParams* par
 template <int LG>
 static cudaError_t pass_b_x2_at(const FitnessPlan& pl, const ParticleParams* params, int64_t p0, int64_t np,
                                 const void* inter, Partial* partials, cudaStream_t s) {
-    constexpr int TB = x2_b_tb(LG);
+    constexpr int TB = pass_b_tb(LG, 4);
     const size_t smem = sizeof(c32x2) * (size_t)TB * fft16_buf_elems(LG);
     auto kern = pass_b_x2_kernel<LG>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-#if FCAS_X2_CARVEOUT
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-    if (e != cudaSuccess) return e;
-#endif
     dim3 grid((unsigned)((1 << pl.log_n2) / TB), (unsigned)np);
     kern<<<grid, x2_b_threads(LG), smem, s>>>(static_cast<const c32x2*>(inter), params, p0, pl.log_n2, pl.n_samples,
                                               static_cast<const float2*>(pl.stw_b), partials);

@@ -17,9 +17,6 @@
 
 #include <cuda_runtime.h>
 
-#ifndef FCAS_X2_ROT_SCALAR
-#define FCAS_X2_ROT_SCALAR 0
-#endif
 
 namespace fcas {
 
@@ -111,27 +108,15 @@ __device__ __forceinline__ c32x2 rot16_x2(c32x2 x) {
         constexpr float ca = (m == 1 || m == 15) ? kC8 : (m == 3 || m == 13) ? kS8 : (m == 5 || m == 11) ? -kS8 : -kC8;
         constexpr float sa = (m == 1 || m == 7) ? kS8 : (m == 3 || m == 5) ? kC8 : (m == 9 || m == 15) ? -kS8 : -kC8;
         constexpr float c = ca, s = S > 0 ? sa : -sa;
-#if FCAS_X2_ROT_SCALAR
-        // scalar FP32 on the halves with the constants as immediate operands (packed operands would
-        // need the three constant pairs in registers)
-        return cmul(x, make_float2(c, s));
-#else
         const f32x2 vc = bcast2(c), vs = bcast2(s), vns = bcast2(-s);
         return c32x2{fma2(x.y, vns, x.x * vc), fma2(x.y, vc, x.x * vs)};
-#endif
     }
 }
 
-// read-only loads that do not allocate in L1 (data read once per SM: the intermediate rows of pass B,
-// the whitened spectrum of pass A)
+// read-only load that does not allocate in L1 (pass B reads each intermediate element once)
 __device__ __forceinline__ c32x2 ld_na(const c32x2* p) {
     c32x2 r;
     asm("ld.global.nc.L1::no_allocate.v2.b64 {%0, %1}, [%2];" : "=l"(r.x.v), "=l"(r.y.v) : "l"(p));
-    return r;
-}
-__device__ __forceinline__ float2 ld_na(const float2* p) {
-    float2 r;
-    asm("ld.global.nc.L1::no_allocate.v2.f32 {%0, %1}, [%2];" : "=f"(r.x), "=f"(r.y) : "l"(p));
     return r;
 }
 // streamed store (evict-first): pass A's output is read back once, by pass B
