@@ -168,7 +168,7 @@ class ClockSampler:
 # ------------------------------------------------------------------------------------------- roofline
 FITNESS_KERNEL_SOURCES = ["paper_2002_02150_gb300/csrc/fcas_passes.cuh", "paper_2002_02150_gb300/csrc/fcas_kernels.cuh",
                           "paper_2002_02150_gb300/csrc/fcas_fft16.cuh", "paper_2002_02150_gb300/csrc/fcas_internal.cuh",
-                          "include/fcas.h"]
+                          "paper_2002_02150_gb300/csrc/fcas_x2.cuh", "include/fcas.h"]
 
 
 def _code_only(text):
