@@ -307,9 +307,10 @@ typedef struct fcas_group fcas_group;
 /*
  * fcas_set_shape -- pin the launch shape without timing: split_bias 0 or 1, k1b one of the compiled
  * pass-A widths for the resulting length (0 = default), sub a power of two, radix_bits_a 4 (radix-16
- * stages), 3 (radix-8 stages, float-float form only, for 2^10..2^12-point columns with k1b = 2) or 0
- * (the default of the form and length: radix 8 for the float-float form's 2^11-point columns, radix 16
- * otherwise).
+ * stages), 3 (radix-8 stages: the FP32 form's 2^10..2^11-point columns with k1b = 4 and
+ * 2^10..2^12-point columns with k1b = 2; the float-float form's 2^10..2^12-point columns with
+ * k1b = 2; not the binary64 form) or 0 (the default of the form and length: radix 8 for the
+ * float-float form's 2^11-point columns, radix 16 otherwise).
  * FCAS_ERR_INVALID for a shape that is not available. Synchronous.
  */
 int fcas_set_shape(fcas_ctx* ctx, int32_t split_bias, int32_t k1b, int32_t sub, int32_t radix_bits_a, void* stream);
