@@ -389,9 +389,13 @@ __global__ void layout_kernel(const double2* __restrict__ ynat, int n_det, int l
             b53 = b1 * b23;
         }
         if (precision == FCAS_PREC_FP32) {
+            // phi^-1/3 at every bin but DC, in the band and outside it (where the spectrum is zero): the
+            // packed pass A forms the phase of the bins next to an anchor bin from the anchor's powers,
+            // and the anchor of the band's lowest bins lies just below the band
+            const double b13f = k >= k_lo && k <= k_hi ? b13 : k > 0 ? cbrt(f_star / ((double)k * df)) : 0.0;
             BasisF bf;
-            bf.h = (float)b13;
-            bf.l = (float)(b13 - (double)bf.h);
+            bf.h = (float)b13f;
+            bf.l = (float)(b13f - (double)bf.h);
             static_cast<BasisF*>(basis)[g] = bf;
         } else {
             BasisD bd;

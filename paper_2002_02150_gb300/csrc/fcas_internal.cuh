@@ -62,7 +62,8 @@ struct ParticleParams {
     float dh[FCAS_MAX_DET], dl[FCAS_MAX_DET];
     float w1f[FCAS_MAX_DET], w2f[FCAS_MAX_DET];
     int32_t valid;                 // 0: non-finite / non-positive input -> fitness NaN, tc -1
-    int32_t pad;
+    int32_t taylor_ok;             // FP32 pass A may step the chirp phase from an anchor bin to the
+                                   // next 3 bins (second-order remainder below 1e-7 turns)
 };
 
 // ------------------------------------------------------------------------------------------

@@ -505,6 +505,9 @@ pass_a_x2_kernel(const float2* __restrict__ y, const BasisF* __restrict__ basis,
     extern __shared__ __align__(16) unsigned char smem_raw[];
     c32x2* smem = reinterpret_cast<c32x2*>(smem_raw);
     __shared__ DetConst<float> sc;
+    // the chirp phase from anchor bins shared by the lanes of adjacent columns (K1B of 2 or 4)
+    constexpr bool kLane = K1B >= 2 && K1B <= 4 && VH % K1B == 0;
+    constexpr int kAnch = kLane ? VH / K1B : VH;   // basis loads (anchor bins) per lane
     __shared__ float scc[2][4];   // chirp-phase coefficients (hi, lo) of the item's particle
 
     const int c = threadIdx.x % K1B;
@@ -521,13 +524,23 @@ pass_a_x2_kernel(const float2* __restrict__ y, const BasisF* __restrict__ basis,
         const ParticleParams* pp = params + p0 + p;
         // the chirp basis and the first detector's spectrum of the thread's bins do not depend on the
         // particle: requested before its constants, so that the two round trips overlap
-        const int64_t bidx0 = ((int64_t)blk * (L / 2) + j) * K1B + c;
-        const BasisF* bb = basis + bidx0;
-        BasisF bq[VH];
+        BasisF bq[kAnch];
+        if constexpr (kLane) {
+            // the basis of the lane's anchor bins: the lane group's first column (K1B blk) at
+            // q = c kAnch + a
+            const int64_t bidx0 = ((int64_t)blk * (L / 2) + j) * K1B;
 #pragma unroll
-        for (int q = 0; q < VH; ++q)
-            if (FCAS_CHECK(bidx0 + (int64_t)q * G * K1B < ((int64_t)L / 2 << log_n1), kCheckBasis))
-                bq[q] = bb[(int64_t)q * G * K1B];
+            for (int a = 0; a < kAnch; ++a) {
+                const int64_t bi = bidx0 + (int64_t)(c * kAnch + a) * G * K1B;
+                if (FCAS_CHECK(bi < ((int64_t)L / 2 << log_n1), kCheckBasis)) bq[a] = basis[bi];
+            }
+        } else {
+            const int64_t bidx0 = ((int64_t)blk * (L / 2) + j) * K1B + c;
+#pragma unroll
+            for (int q = 0; q < VH; ++q)
+                if (FCAS_CHECK(bidx0 + (int64_t)q * G * K1B < ((int64_t)L / 2 << log_n1), kCheckBasis))
+                    bq[q] = basis[bidx0 + (int64_t)q * G * K1B];
+        }
         const int64_t col0 = (int64_t)blk * n_det;
         float2 y0[VH];   // detector 0 (every context has at least one)
         {
@@ -552,6 +565,7 @@ pass_a_x2_kernel(const float2* __restrict__ y, const BasisF* __restrict__ basis,
                 kcl = pp->cl[i];
             }
         }
+        const int taylor_ok = pp->taylor_ok;
         if (!pp->valid) continue;   // not evaluated (invalid input, or a PSO particle outside its box)
         // the particle's constants in shared memory (earlier items' reads of them all ended before
         // the barriers of their transforms)
@@ -611,15 +625,71 @@ pass_a_x2_kernel(const float2* __restrict__ y, const BasisF* __restrict__ basis,
                 cfh[r] = scc[0][r];
                 cfl[r] = scc[1][r];
             }
+            if (kLane && taylor_ok) {
+                // The K1B lanes of a group (consecutive lanes, one per column) hold the adjacent bins
+                // k_a + c (c < K1B) at every q. Lane c forms, at the anchor bins k_a of kAnch values of
+                // q, the phase psi (turns: float-float products reduced mod 1) and in FP32 from the same
+                // powers b_m = phi^-e_m (e_m = 5/3, 1, 2/3, 1/3) its derivatives along k:
+                //   psi' = -(1/k) sum_m e_m c_m b_m,   psi'' = (1/k^2) sum_m e_m (e_m + 1) c_m b_m.
+                // The group exchanges them and each lane steps to its own bin by
+                //   psi(k_a + c) = psi(k_a) + c psi' + c^2 psi''/2;
+                // taylor_ok (set by the geometry kernel) bounds the remainder below 1e-7 turns for the
+                // particle; otherwise every bin's phase is formed from its own powers.
+                float sa[kAnch], d1a[kAnch], d2a[kAnch];
 #pragma unroll
-            for (int q = 0; q < VH; ++q) {
-                const ChirpPowers b = chirp_powers_lean(bq[q]);
-                float s = frac_mul_ff(cfh[0], cfl[0], b.b53.x, b.b53.y);
-                s += frac_mul_ff(cfh[1], cfl[1], b.b1.x, b.b1.y);
-                s += frac_mul_ff(cfh[2], cfl[2], b.b23.x, b.b23.y);
-                s += frac_mul_ff(cfh[3], cfl[3], b.b13.x, b.b13.y);
-                const float2 cp = fast_phasor(s - rintf(s));
-                v[q] = pack_series(cmul(r1[q], cp), cmul(r2[q], cp));
+                for (int a = 0; a < kAnch; ++a) {
+                    const ChirpPowers b = chirp_powers_lean(bq[a]);
+                    float s = frac_mul_ff(cfh[0], cfl[0], b.b53.x, b.b53.y);
+                    s += frac_mul_ff(cfh[1], cfl[1], b.b1.x, b.b1.y);
+                    s += frac_mul_ff(cfh[2], cfl[2], b.b23.x, b.b23.y);
+                    s += frac_mul_ff(cfh[3], cfl[3], b.b13.x, b.b13.y);
+                    const float g1 =
+                        fmaf(cfh[0] * (5.0f / 3.0f), b.b53.x,
+                             fmaf(cfh[1], b.b1.x, fmaf(cfh[2] * (2.0f / 3.0f), b.b23.x, cfh[3] * (1.0f / 3.0f) * b.b13.x)));
+                    const float g2 =
+                        fmaf(cfh[0] * (40.0f / 9.0f), b.b53.x,
+                             fmaf(cfh[1] * 2.0f, b.b1.x, fmaf(cfh[2] * (10.0f / 9.0f), b.b23.x, cfh[3] * (4.0f / 9.0f) * b.b13.x)));
+                    const float ka = (float)(blk * K1B + n1 * (j + (c * kAnch + a) * G));   // < 2^24: exact
+                    const float rk = ka > 0.0f ? __frcp_rn(ka) : 0.0f;   // the DC bin carries no phase
+                    sa[a] = s;
+                    d1a[a] = -g1 * rk;
+                    d2a[a] = 0.5f * g2 * rk * rk;
+                }
+                const int lane0 = (threadIdx.x & 31) - c;   // the group's first lane
+                const float cf = (float)c;
+#pragma unroll
+                for (int q = 0; q < VH; ++q) {
+                    const int src = lane0 + q / kAnch;
+                    const float s0 = __shfl_sync(0xffffffffu, sa[q % kAnch], src);
+                    const float d1 = __shfl_sync(0xffffffffu, d1a[q % kAnch], src);
+                    const float d2 = __shfl_sync(0xffffffffu, d2a[q % kAnch], src);
+                    const float s = fmaf(cf, fmaf(cf, d2, d1), s0);
+                    const float2 cp = fast_phasor(s - rintf(s));
+                    v[q] = pack_series(cmul(r1[q], cp), cmul(r2[q], cp));
+                }
+            } else {
+                // every bin from its own basis entry (requested here when only the anchors' were)
+                BasisF bo[VH];
+                if constexpr (kLane) {
+                    const int64_t bidx0 = ((int64_t)blk * (L / 2) + j) * K1B + c;
+#pragma unroll
+                    for (int q = 0; q < VH; ++q)
+                        if (FCAS_CHECK(bidx0 + (int64_t)q * G * K1B < ((int64_t)L / 2 << log_n1), kCheckBasis))
+                            bo[q] = basis[bidx0 + (int64_t)q * G * K1B];
+                } else {
+#pragma unroll
+                    for (int q = 0; q < VH; ++q) bo[q] = bq[q < kAnch ? q : 0];
+                }
+#pragma unroll
+                for (int q = 0; q < VH; ++q) {
+                    const ChirpPowers b = chirp_powers_lean(bo[q]);
+                    float s = frac_mul_ff(cfh[0], cfl[0], b.b53.x, b.b53.y);
+                    s += frac_mul_ff(cfh[1], cfl[1], b.b1.x, b.b1.y);
+                    s += frac_mul_ff(cfh[2], cfl[2], b.b23.x, b.b23.y);
+                    s += frac_mul_ff(cfh[3], cfl[3], b.b13.x, b.b13.y);
+                    const float2 cp = fast_phasor(s - rintf(s));
+                    v[q] = pack_series(cmul(r1[q], cp), cmul(r2[q], cp));
+                }
             }
         }
 #pragma unroll
