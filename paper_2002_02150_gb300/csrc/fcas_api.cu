@@ -229,7 +229,7 @@ int ensure_grad(fcas_ctx* c, int64_t n) {
 cudaError_t gradient_device(fcas_ctx* c, int64_t n, const double* d_theta, const int64_t* d_tc, double* d_grad,
                             cudaStream_t st) {
     cudaError_t e = launch_geometry(d_theta, n, c->d_params, c->d_det, c->d_sigma2s, c->setup.n_det, c->setup.f_low,
-                                    c->df, st);
+                                    c->df, pass_a_kstep(c), st);
     if (e != cudaSuccess) return e;
     const FitnessPlan plan = make_plan(c);
     if (c->setup.precision == FCAS_PREC_FP32)
@@ -587,7 +587,7 @@ int fcas_fitness(fcas_ctx* c, int64_t n, const double* theta, double* fitness, i
     size_t slot;
     prof_begin(c, FCAS_KERNEL_GEOMETRY, st, &slot);
     FCAS_CUDA(launch_geometry(d_theta, n, c->d_params, c->d_det, c->d_sigma2s, c->setup.n_det, c->setup.f_low, c->df,
-                              st));
+                              pass_a_kstep(c), st));
     prof_end(c, slot, st);
     FCAS_CUDA(launch_passes(c, n, d_fit, d_tc, st));
     if (!f_dev) FCAS_CUDA(cudaMemcpyAsync(fitness, d_fit, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, st));
@@ -644,7 +644,8 @@ cudaError_t swarm_iteration(fcas_ctx* c, const PsoDev& g, const Swarm& w, Partic
                             Partial* partials, int64_t chunk, int64_t rows, cudaStream_t st) {
     cudaError_t x = launch_pso_theta(g, w.s, w.theta, st);
     if (x == cudaSuccess)
-        x = launch_geometry(w.theta, rows, params, c->d_det, c->d_sigma2s, c->setup.n_det, c->setup.f_low, c->df, st);
+        x = launch_geometry(w.theta, rows, params, c->d_det, c->d_sigma2s, c->setup.n_det, c->setup.f_low, c->df,
+                            pass_a_kstep(c), st);
     if (x == cudaSuccess) x = launch_passes_with(c, params, inter, partials, chunk, rows, w.fit, w.tcs, st);
     if (x == cudaSuccess) x = launch_pso_update(g, 0, w.fit, w.tcs, w.s, st);
     return x;
@@ -773,7 +774,7 @@ int fcas_autotune(fcas_ctx* c, int64_t n_particles, const char* cache_path, void
     }
     FCAS_CUDA(cudaMemcpyAsync(c->d_theta, th.data(), sizeof(double) * th.size(), cudaMemcpyHostToDevice, st));
     FCAS_CUDA(launch_geometry(c->d_theta, n_particles, c->d_params, c->d_det, c->d_sigma2s, c->setup.n_det,
-                              c->setup.f_low, c->df, st));
+                              c->setup.f_low, c->df, pass_a_kstep(c), st));
     cudaEvent_t e0, e1;
     FCAS_CUDA(cudaEventCreate(&e0));
     FCAS_CUDA(cudaEventCreate(&e1));
@@ -1108,7 +1109,8 @@ int fcas_polish(fcas_ctx* c, int64_t n, double* theta, double* fitness, int64_t*
                               th_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
     FCAS_CUDA(cudaMemsetAsync(w_acc, 0, sizeof(int32_t) * (size_t)n, st));
     // the fitness at the starting points
-    FCAS_CUDA(launch_geometry(w_th, n, c->d_params, c->d_det, c->d_sigma2s, c->setup.n_det, c->setup.f_low, c->df, st));
+    FCAS_CUDA(launch_geometry(w_th, n, c->d_params, c->d_det, c->d_sigma2s, c->setup.n_det, c->setup.f_low, c->df,
+                              pass_a_kstep(c), st));
     FCAS_CUDA(launch_passes(c, n, w_fit, w_tc, st));
     for (int32_t step = 0; step < steps; ++step) {
         FCAS_CUDA(gradient_device(c, n, w_th, w_tc, w_grad, st));
@@ -1117,7 +1119,7 @@ int fcas_polish(fcas_ctx* c, int64_t n, double* theta, double* fitness, int64_t*
             FCAS_CUDA(cudaMemsetAsync(w_searching, 0, sizeof(int32_t), st));
             FCAS_CUDA(launch_polish_candidate(w_th, w_dir, w_step, w_done, n, w_cand, st));
             FCAS_CUDA(launch_geometry(w_cand, n, c->d_params, c->d_det, c->d_sigma2s, c->setup.n_det, c->setup.f_low,
-                                      c->df, st));
+                                      c->df, pass_a_kstep(c), st));
             FCAS_CUDA(launch_passes(c, n, w_cfit, w_ctc, st));
             FCAS_CUDA(launch_polish_accept(w_th, w_fit, w_tc, w_cand, w_cfit, w_ctc, w_step, w_done, w_acc, n,
                                            w_searching, st));

@@ -110,6 +110,12 @@ inline cudaError_t launch_pass_b_prec(int precision, const FitnessPlan& plan, co
     return launch_pass_b<double>(plan, params, p0, np, inter, partials, st);
 }
 
+// bin step between a pass-A thread's consecutive values: N1 N2 / V_A, V_A = 2^min(log N2, radix bits)
+inline int64_t pass_a_kstep(const fcas_ctx* c) {
+    const int vb = c->log_n2 < c->radix_bits_a ? c->log_n2 : c->radix_bits_a;
+    return (int64_t)1 << (c->log_n - vb);
+}
+
 inline FitnessPlan make_plan(const fcas_ctx* c) {
     FitnessPlan p;
     p.n_det = c->setup.n_det;

@@ -61,6 +61,8 @@ struct ParticleParams {
     float ch[4], cl[4];
     float dh[FCAS_MAX_DET], dl[FCAS_MAX_DET];
     float w1f[FCAS_MAX_DET], w2f[FCAS_MAX_DET];
+    float2 dstep[FCAS_MAX_DET];    // e^{2 pi i S Delta^i df}, S = N / V_A: the FP32 pass A's step of the
+                                   // delay phasor between a thread's consecutive bins (binary64 phase)
     int32_t valid;                 // 0: non-finite / non-positive input -> fitness NaN, tc -1
     int32_t taylor_ok;             // FP32 pass A may step the chirp phase from an anchor bin to the
                                    // next 3 bins (second-order remainder below 1e-7 turns)

@@ -11,7 +11,7 @@ namespace fcas {
 // ------------------------------------------------------------------------------------------
 __global__ void geometry_kernel(const double* __restrict__ theta, int64_t n, ParticleParams* __restrict__ out,
                                 const double* __restrict__ det9, const double* __restrict__ s2, int n_det,
-                                double f_star, double df) {
+                                double f_star, double df, int64_t kstep) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     const double alpha = theta[4 * p + 0], delta = theta[4 * p + 1];
@@ -118,16 +118,23 @@ __global__ void geometry_kernel(const double* __restrict__ theta, int64_t n, Par
         pp.dl[i] = (float)(pp.dturn[i] - (double)pp.dh[i]);
         pp.w1f[i] = (float)pp.w1[i];
         pp.w2f[i] = (float)pp.w2[i];
+        double u = (double)kstep * pp.dturn[i];   // |u| < 2^24 turns, exact to ~1e-9
+        u -= rint(u);
+        double su, cu;
+        sincospi(2.0 * u, &su, &cu);
+        pp.dstep[i] = make_float2((float)cu, (float)su);
     }
     out[p] = pp;
 }
 
 cudaError_t launch_geometry(const double* theta, int64_t n, ParticleParams* out, const double* det9,
-                            const double* sigma2_scaled, int n_det, double f_star, double df, cudaStream_t s) {
+                            const double* sigma2_scaled, int n_det, double f_star, double df, int64_t kstep,
+                            cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     const int threads = 128;
     const int64_t blocks = (n + threads - 1) / threads;
-    geometry_kernel<<<(unsigned)blocks, threads, 0, s>>>(theta, n, out, det9, sigma2_scaled, n_det, f_star, df);
+    geometry_kernel<<<(unsigned)blocks, threads, 0, s>>>(theta, n, out, det9, sigma2_scaled, n_det, f_star, df,
+                                                          kstep);
     return cudaGetLastError();
 }
 

@@ -106,8 +106,9 @@ struct FitnessPlan {
 };
 
 // Per-particle geometry (binary64): chirp coefficients, delays, antenna patterns, G^-1.
+// kstep: the bin step between a pass-A thread's consecutive values (N / V_A, pass_a_kstep).
 cudaError_t launch_geometry(const double* theta, int64_t n, ParticleParams* out, const double* det9,
-                            const double* sigma2_scaled, int n_det, double f_star, double df,
+                            const double* sigma2_scaled, int n_det, double f_star, double df, int64_t kstep,
                             cudaStream_t s);
 
 // Pass A for particles [p0, p0 + np): writes the intermediate [np][2][N2][N1].

@@ -93,7 +93,7 @@ extern "C" int fcas_fitness_noalloc(const fcas_ctx* c, int64_t n, const double* 
     for (int64_t p0 = 0; p0 < n && e == cudaSuccess; p0 += cap) {
         const int64_t np = (n - p0) < cap ? (n - p0) : cap;
         e = launch_geometry(theta + 4 * p0, np, params, c->d_det, c->d_sigma2s, c->setup.n_det, c->setup.f_low, c->df,
-                            st);
+                            pass_a_kstep(c), st);
         if (e == cudaSuccess)
             e = launch_pass_a_prec(c->setup.precision, plan, params, 0, np, inter, st);
         if (e == cudaSuccess) e = launch_pass_b_prec(c->setup.precision, plan, params, 0, np, inter, partials, st);
