@@ -143,7 +143,7 @@ int fcas_fitness(fcas_ctx* ctx, int64_t n, const double* theta, double* fitness,
  * then holds until the process exits. Make that first call during the caller's set-up phase, with
  * the context's device current and before any stream capture; from then on the call allocates
  * nothing. One particle needs 2 * n_fft * (8 bytes FP32, 16 bytes FP64 and float-float) plus
- * ~0.5 KB; particles are processed in chunks that fit. A context whose single particle does not fit
+ * ~0.6 KB; particles are processed in chunks that fit. A context whose single particle does not fit
  * (n_fft >= 2^21 in FP32, >= 2^20 in the other forms) is rejected with FCAS_ERR_INVALID and a
  * message naming the sizes.
  *
