@@ -65,7 +65,7 @@ struct ParticleParams {
                                    // delay phasor between a thread's consecutive bins (binary64 phase)
     int32_t valid;                 // 0: non-finite / non-positive input -> fitness NaN, tc -1
     int32_t taylor_ok;             // FP32 pass A may step the chirp phase from an anchor bin to the
-                                   // next 3 bins (second-order remainder below 1e-7 turns)
+                                   // next 3 (bit 0) or 7 (bit 1) bins: remainder below 1e-7 turns
 };
 
 // ------------------------------------------------------------------------------------------

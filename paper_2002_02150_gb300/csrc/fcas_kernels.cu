@@ -94,18 +94,21 @@ __global__ void geometry_kernel(const double* __restrict__ theta, int64_t n, Par
         pp.c[2] = -1.5 * f_star * tau15;
         pp.c[3] = 3.0 * f_star * tau2;
         pp.valid = 1;
-        // Remainder of psi(k + c) = psi(k) + c psi' + c^2 psi''/2 for c <= 3 (FP32 pass A, adjacent
-        // columns): at most 27/6 max |psi'''| over the band, taken at k_b = f_*/df - 8 (the band's
-        // lowest bin, less the 3 by which an anchor bin may lie below it, with margin), where
-        // |psi'''| <= sum_m |c_m| e_m (e_m + 1) (e_m + 2) phi^-e_m / k^3.
-        const double kb = f_star / df - 8.0;
-        if (kb >= 1.0) {
+        // Remainder of psi(k + c) = psi(k) + c psi' + c^2 psi''/2 for c <= C (FP32 pass A, C + 1
+        // adjacent columns per lane group, C = 3 or 7): at most C^3/6 max |psi'''| over the band,
+        // taken at k_b = f_*/df - 2 (C + 1) (the band's lowest bin, less the C by which an anchor bin
+        // may lie below it, with margin), where |psi'''| <= sum_m |c_m| e_m (e_m + 1) (e_m + 2)
+        // phi^-e_m / k^3. Bit 0: C = 3; bit 1: C = 7.
+        for (int bit = 0; bit < 2; ++bit) {
+            const double cm = bit == 0 ? 3.0 : 7.0;
+            const double kb = f_star / df - 2.0 * (cm + 1.0);
+            if (kb < 1.0) continue;
             const double r = f_star / (kb * df);   // phi^-1 at k_b
             const double r13 = cbrt(r);
             const double d3 = (fabs(pp.c[0]) * (440.0 / 27.0) * r * r13 * r13 + fabs(pp.c[1]) * 6.0 * r +
                                fabs(pp.c[2]) * (80.0 / 27.0) * r13 * r13 + fabs(pp.c[3]) * (28.0 / 27.0) * r13) /
                               (kb * kb * kb);
-            pp.taylor_ok = 4.5 * d3 < 1e-7 ? 1 : 0;
+            if (cm * cm * cm / 6.0 * d3 < 1e-7) pp.taylor_ok |= 1 << bit;
         }
     }
     for (int r = 0; r < 4; ++r) {

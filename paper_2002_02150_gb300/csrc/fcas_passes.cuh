@@ -504,8 +504,8 @@ pass_a_x2_kernel(const float2* __restrict__ y, const BasisF* __restrict__ basis,
     constexpr int VH = V / 2;    // values with k2 < L/2; the rest of the column is zero (k >= N/2)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     c32x2* smem = reinterpret_cast<c32x2*>(smem_raw);
-    // the chirp phase from anchor bins shared by the lanes of adjacent columns (K1B of 2 or 4)
-    constexpr bool kLane = K1B >= 2 && K1B <= 4 && VH % K1B == 0;
+    // the chirp phase from anchor bins shared by the lanes of adjacent columns (K1B of 2, 4 or 8)
+    constexpr bool kLane = K1B >= 2 && K1B <= 8 && VH % K1B == 0;
     constexpr int kAnch = kLane ? VH / K1B : VH;   // basis loads (anchor bins) per lane
 
     const int c = threadIdx.x % K1B;
@@ -599,7 +599,7 @@ pass_a_x2_kernel(const float2* __restrict__ y, const BasisF* __restrict__ basis,
                 cfh[r] = __ldg(&pp->ch[r]);
                 cfl[r] = __ldg(&pp->cl[r]);
             }
-            if (kLane && taylor_ok) {
+            if (kLane && (taylor_ok & (K1B <= 4 ? 1 : 2))) {
                 // The K1B lanes of a group (consecutive lanes, one per column) hold the adjacent bins
                 // k_a + c (c < K1B) at every q. Lane c forms, at the anchor bins k_a of kAnch values of
                 // q, the phase psi (turns: float-float products reduced mod 1) and in FP32 from the same
@@ -607,8 +607,9 @@ pass_a_x2_kernel(const float2* __restrict__ y, const BasisF* __restrict__ basis,
                 //   psi' = -(1/k) sum_m e_m c_m b_m,   psi'' = (1/k^2) sum_m e_m (e_m + 1) c_m b_m.
                 // The group exchanges them and each lane steps to its own bin by
                 //   psi(k_a + c) = psi(k_a) + c psi' + c^2 psi''/2;
-                // taylor_ok (set by the geometry kernel) bounds the remainder below 1e-7 turns for the
-                // particle; otherwise every bin's phase is formed from its own powers.
+                // taylor_ok (set by the geometry kernel: bit 0 for steps of up to 3 bins, bit 1 up to 7)
+                // bounds the remainder below 1e-7 turns for the particle; otherwise every bin's phase
+                // is formed from its own powers.
                 float sa[kAnch], d1a[kAnch], d2a[kAnch];
 #pragma unroll
                 for (int a = 0; a < kAnch; ++a) {

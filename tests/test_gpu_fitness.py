@@ -336,29 +336,29 @@ def test_null_psd_is_the_analytic_aligo_fit(precision):
     assert_parity(oracle_setup(w, data), theta, f0, t0, precision, "psd=NULL")
 
 
-@pytest.mark.parametrize("radix_bits", [4, 3])
-def test_shared_chirp_phase_and_its_per_particle_fallback(radix_bits):
-    """FP32 pass A with four columns per CTA steps the chirp phase of adjacent bins from anchor bins
-    only for particles whose second-order remainder bound is below 1e-7 turns, and forms every bin
-    itself for the others. A 128-s segment whose band starts at bin 5376 (42 Hz) puts the bound's
-    threshold inside the chirp-time box: the five particles at the box's lowest tau0 qualify (bound
-    0.81-0.85e-7 turns), the five above it do not (1.09e-7 and more). One launch holds both kinds,
-    each checked against the oracle."""
+@pytest.mark.parametrize("k1b,radix_bits,f_low,cmax", [(4, 4, 42.0, 3), (4, 3, 42.0, 3), (8, 4, 90.0, 7)])
+def test_shared_chirp_phase_and_its_per_particle_fallback(k1b, radix_bits, f_low, cmax):
+    """FP32 pass A with four (eight) columns per CTA steps the chirp phase of adjacent bins from
+    anchor bins only for particles whose remainder bound for steps of up to 3 (7) bins is below 1e-7
+    turns, and forms every bin itself for the others. A 128-s segment whose band starts at 42 Hz
+    (90 Hz) puts the bound's threshold inside the chirp-time box: the particles at the box's lowest
+    tau0 qualify, those above do not. One launch holds both kinds, each checked against the oracle."""
     import paper_2002_02150_gb300 as fc
     from test_taylor_bound import bound, coefficients
     w = dataclasses.replace(sd.C1, name="4det-128s-8192Hz", fs=8192.0, n_fft=1 << 20, n_samples=(1 << 20) - 4321,
-                            f_low=42.0, f_high=400.0, arrival_s=40.0)
+                            f_low=f_low, f_high=400.0, arrival_s=40.0)
     data = sd.make_dataset(w, 11)
     rng = np.random.default_rng(11)
     t0lo, t0hi, t15lo, t15hi = sd.chirp_time_box(w.f_low)
-    tau0 = np.concatenate([np.linspace(t0lo, t0lo + 0.25, 5), np.linspace(t0lo + 2.0, t0hi, 5)])
+    span = (t0hi - t0lo) / 36.0   # 1 s at 42 Hz
+    tau0 = np.concatenate([np.linspace(t0lo, t0lo + 0.25 * span, 5), np.linspace(t0lo + 2.0 * span, t0hi, 5)])
     tau15 = rng.uniform(t15lo, t15hi, tau0.size)
     theta = np.stack([rng.uniform(0, 2 * np.pi, tau0.size), np.arcsin(rng.uniform(-1, 1, tau0.size)), tau0, tau15], 1)
     df = w.fs / w.n_fft
-    shared = [bound(coefficients(a, b, w.f_low), w.f_low, df) < 1e-7 for a, b in zip(tau0, tau15)]
+    shared = [bound(coefficients(a, b, w.f_low), w.f_low, df, cmax) < 1e-7 for a, b in zip(tau0, tau15)]
     assert any(shared) and not all(shared), shared
     with make_ctx(w, data, "fp32") as ctx:
-        info = fc.fcas_set_shape(ctx, 0, 4, 8, radix_bits)
-        assert info["k1b"] == 4 and info["radix_bits_a"] == radix_bits
+        info = fc.fcas_set_shape(ctx, 0, k1b, 8, radix_bits)
+        assert info["k1b"] == k1b and info["radix_bits_a"] == radix_bits
         fit, tc = gpu_fitness(ctx, theta)
-    assert_parity(oracle_setup(w, data), theta, fit, tc, "fp32", f"shared chirp phase, radix bits {radix_bits}")
+    assert_parity(oracle_setup(w, data), theta, fit, tc, "fp32", f"shared chirp phase, K1B {k1b}, radix bits {radix_bits}")
