@@ -746,11 +746,14 @@ pass_b_x2_kernel(const c32x2* __restrict__ inter, const ParticleParams* __restri
     // comparison keeps the lowest t among equal values
     float best = -1.0f;
     int bt = INT_MAX;
+    // the lag bound in 32 bits (t < N <= 2^24): one comparison per value instead of a 64-bit one
+    // (60-min pass B 1.95 -> 1.87 ms per 64 particles)
+    const int ns = n_samples < (int64_t)INT_MAX ? (int)n_samples : INT_MAX;
 #pragma unroll
     for (int q = 0; q < V; ++q) {
         const int t = ta + n2 * (j + q * G);
         const float g = norm2_sum(v[q]);
-        if (t < n_samples && g > best) {
+        if (t < ns && g > best) {
             best = g;
             bt = t;
         }
