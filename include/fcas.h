@@ -48,7 +48,10 @@ enum fcas_status {
 enum fcas_precision {
     FCAS_PREC_FP64 = 0,      /* plain form: phase, products, FFTs and projection in binary64 */
     FCAS_PREC_FP32 = 1,      /* FP32 products/FFTs/projection; chirp and delay phase as
-                                float-float (hi + lo) values reduced mod 1 turn */
+                                float-float (hi + lo) values reduced mod 1 turn (the delay
+                                phasors' per-particle step in binary64; adjacent bins' chirp
+                                phase stepped from a shared bin where the step's error is
+                                below 1e-7 turns) */
     FCAS_PREC_FF = 2         /* binary64-class accuracy on the FP32 units: phase and detector sums
                                 in binary64, transforms and projection in float-float (double-word)
                                 arithmetic; spectrum, tables and intermediate as in the binary64 form */
