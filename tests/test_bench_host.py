@@ -77,3 +77,20 @@ def test_oracle_judgements_report_fitness_and_argmax():
     setup = o.OracleSetup(data["det"], data["psd"], data["data"], w.n_fft, w.fs, w.f_low, w.f_high)
     for (v, t), p in zip(got["pts"], th):
         assert (v, t) == o.fitness(setup, p)
+
+
+def test_traffic_record_is_the_stated_scaling_of_its_capture():
+    """The committed DRAM record holds 64-particle launches scaled from 8-particle captures of one
+    kernel each: pass A's spectrum and basis reads once per launch, its intermediate writes times 8;
+    pass B's intermediate reads times 8, its writes as captured. Both records come from one set of
+    kernel sources, and each read/write is at least the algorithmic bytes of what it scales."""
+    rec = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))["4det-60min-2048Hz"]
+    a, b = rec["pass_a"], rec["pass_b"]
+    assert a["kernel_hash"] == b["kernel_hash"]
+    scale = a["particles_per_launch"] // a["captured"]["particles"]
+    assert scale == 8 and b["particles_per_launch"] // b["captured"]["particles"] == scale
+    assert a["read"] == a["captured"]["read"] and a["write"] == scale * a["captured"]["write"]
+    assert b["read"] == scale * b["captured"]["read"] and b["write"] == b["captured"]["write"]
+    per_particle = (1 << 23) * 16                      # one particle's intermediate, FP32 form
+    assert 0.9 * 64 * per_particle <= a["write"] <= 1.01 * 64 * per_particle
+    assert 64 * per_particle <= b["read"] <= 1.01 * 64 * per_particle
